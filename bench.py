@@ -1,0 +1,528 @@
+#!/usr/bin/env python
+"""Benchmark of the AGIS counting hot path on B300 (one JSON line on stdout).
+
+Workload (plain per-query launches): R-MAT scale 22 (4.2M vertices, edge factor
+16, a=0.57 b=0.19 c=0.19, symmetrised, deduplicated, int32 columns), patterns
+4-clique, 5-cycle, house and 5-clique, 2^28 trials each under the decision
+function D^pi (beta = 0.8), FP64 estimate and variance.  One step is one pass
+of the whole path over that input: Sec. 4.4 preprocessing (neighbour-degree sums
+and sampled clustering coefficients), the f_approx weight tables and prefix
+sums, 2^28 Alg. 3 trials per pattern with per-tile FP64 reductions, and the
+final sums.  Inputs are synthetic; the paper's data sets are not available.
+
+Also reported: the same metric end to end through the C ABI from host buffers
+(`e2e`), time to +-1% error at 95% confidence (Alg. 1, eps = 0.01, delta = 0.05)
+for plain, batched and served forms, the sampler kernel's achieved bandwidth
+against the measured HBM copy peak (`roofline`), and the CPU oracle on a bounded
+sample of the same workload on this host's cores (`cpu_baseline`).
+
+--impl reference times the CPU oracle instead (the reference arm of this
+repository; the paper's own code is not available here).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "samples/s & time-to-±1% err (95% CI), batched/served vs plain, 1 B300"
+PATTERN_NAMES = ["4-clique", "5-cycle", "house", "5-clique"]
+CMIN = 2.0 ** -10
+TILE = 1024
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="agis", choices=["agis", "reference"])
+    ap.add_argument("--scale", type=int, default=22)
+    ap.add_argument("--log2-trials", type=int, default=28)
+    ap.add_argument("--patterns", default=",".join(PATTERN_NAMES))
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-tte", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--json-out", default="")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ distributed (replicas only)
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce_max(x, world):
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples during the timed region."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def start(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+# ------------------------------------------------------------------ inputs
+
+def make_workload(scale):
+    from paper_2601_01388_b300 import inputs as I
+    t = time.time()
+    off, cols = I.rmat_graph(scale, 16, 0.57, 0.19, 0.19, seed=1)
+    return off, cols, time.time() - t
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+def profile_traffic(trials_per_launch):
+    """DRAM bytes per trial of the sampler from the committed ncu summary, if it was
+    taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "sample_kernel_rmat_s22.md")
+    src = os.path.join(ROOT, "paper_2601_01388_b300", "csrc", "sample.cu")
+    if not os.path.exists(path):
+        return None
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    text = open(path).read()
+    if f"sample.cu sha256[:16]: {h}" not in text:
+        return None
+    for line in text.splitlines():
+        if line.strip().startswith("dram_bytes_per_trial:"):
+            return float(line.split(":")[1].split()[0]) * trials_per_launch
+    return None
+
+
+# ------------------------------------------------------------------ CPU oracle
+
+_ORC = {}
+
+
+def _orc_init(shm_names, nv, nnz, nsum_name, hits_name):
+    from multiprocessing import shared_memory
+    from oracle import oracle as O
+    O.build()
+    shms = [shared_memory.SharedMemory(name=n) for n in shm_names + [nsum_name, hits_name]]
+    _ORC["shms"] = shms
+    _ORC["off"] = np.ndarray((nv + 1,), dtype=np.int64, buffer=shms[0].buf)
+    _ORC["cols"] = np.ndarray((nnz,), dtype=np.int32, buffer=shms[1].buf)
+    _ORC["nsum"] = np.ndarray((nv,), dtype=np.uint64, buffer=shms[2].buf)
+    _ORC["hits"] = np.ndarray((nv,), dtype=np.uint32, buffer=shms[3].buf)
+    _ORC["O"] = O
+
+
+def _orc_stats(v0, v1):
+    O = _ORC["O"]
+    O.graph_stats_range(_ORC["off"], _ORC["cols"], 1, v0, v1, _ORC["nsum"], _ORC["hits"])
+    return v1 - v0
+
+
+def _orc_sample(name, seed, first, count):
+    from paper_2601_01388_b300 import inputs as I
+    O = _ORC["O"]
+    key = (name, seed)
+    q = _ORC.get(key)
+    if q is None:
+        k, edges = I.PATTERNS[name]
+        q = O.Query(_ORC["off"], _ORC["cols"], k, edges, nsum=_ORC["nsum"], hits=_ORC["hits"],
+                    c_min=CMIN, mode=0, seed=seed)
+        _ORC[key] = q
+    t = time.time()
+    s = q.sums(first, count)
+    return count, time.time() - t, s["sum_x"]
+
+
+class OraclePool:
+    """The CPU oracle on all host cores: one spawn-started process per core, the CSR
+    in shared memory, preprocessing split by vertex ranges and sampling split by
+    disjoint trial ranges (the results are the single-process results)."""
+
+    def __init__(self, off, cols, procs=None):
+        import multiprocessing as mp
+        from multiprocessing import shared_memory
+        self.nv, self.nnz = len(off) - 1, len(cols)
+        self.procs = procs or os.cpu_count() or 1
+        self.shm = []
+        arrs = []
+        for a in (off, cols):
+            s = shared_memory.SharedMemory(create=True, size=max(a.nbytes, 1))
+            np.ndarray(a.shape, dtype=a.dtype, buffer=s.buf)[:] = a
+            self.shm.append(s)
+        for dt in (np.uint64, np.uint32):
+            s = shared_memory.SharedMemory(create=True, size=max(self.nv * np.dtype(dt).itemsize, 1))
+            self.shm.append(s)
+            arrs.append(s)
+        ctx = mp.get_context("spawn")
+        self.pool = ctx.Pool(self.procs, initializer=_orc_init,
+                             initargs=([self.shm[0].name, self.shm[1].name], self.nv, self.nnz,
+                                       self.shm[2].name, self.shm[3].name))
+
+    def preprocess(self):
+        t = time.time()
+        parts = max(1, self.procs * 8)
+        step = (self.nv + parts - 1) // parts
+        ranges = [(v, min(self.nv, v + step)) for v in range(0, self.nv, step)]
+        self.pool.starmap(_orc_stats, ranges)
+        return time.time() - t
+
+    def sample(self, names, per_pattern, seed_base=1):
+        """per_pattern trials of each pattern, split across processes; returns
+        (trials, wall seconds)."""
+        jobs = []
+        chunk = max(1, per_pattern // self.procs)
+        for i, n in enumerate(names):
+            for first in range(0, per_pattern, chunk):
+                jobs.append((n, seed_base + i, first, min(chunk, per_pattern - first)))
+        t = time.time()
+        res = self.pool.starmap(_orc_sample, jobs)
+        return sum(r[0] for r in res), time.time() - t
+
+    def close(self):
+        self.pool.terminate()
+        for s in self.shm:
+            s.close()
+            s.unlink()
+
+
+def cpu_rate(pool, names, seconds):
+    """Samples/s of the oracle on a bounded sample sized to about `seconds`."""
+    per = max(pool.procs, 64)
+    n, dt = pool.sample(names, per)            # warms every process's query state
+    while dt < seconds / 4 and per < (1 << 26):
+        per *= 4
+        n, dt = pool.sample(names, per)
+    return n / dt, n, dt, per
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def run_gpu(args, world, rank, local):
+    import torch
+    from paper_2601_01388_b300 import build
+    build.build()
+    from paper_2601_01388_b300 import agis
+    from paper_2601_01388_b300 import inputs as I
+
+    names = [n for n in args.patterns.split(",") if n]
+    trials = 1 << args.log2_trials
+    ntiles = (trials + TILE - 1) // TILE
+    off, cols, t_gen = make_workload(args.scale)
+
+    pool = None
+    want_cpu = (rank == 0 and world == 1 and not args.no_cpu)
+    if want_cpu:
+        pool = OraclePool(off, cols)              # spawn-started processes
+
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    ctx = agis.Context(local, stream.cuda_stream)
+    with torch.cuda.stream(stream):
+        g = agis.Graph(ctx, off, cols, validate=True)
+        info = g.info()
+        pats = [agis.Pattern(*I.PATTERNS[n]) for n in names]
+        opts = [agis.default_opts(mode=0, seed=1 + i, eps=0.0, max_trials=trials) for i in range(len(names))]
+        outs = [torch.zeros(ntiles * 4, dtype=torch.int64, device="cuda") for _ in names]
+
+        def step(record):
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3 + 2 * len(names))]
+            ev[0].record(stream)
+            g.preprocess(1, CMIN)                           # a1, a2 (Sec. 4.4)
+            ev[1].record(stream)
+            for p, o in zip(pats, opts):                    # a3, a4 (tables + prefix sums)
+                agis.prepare(g, p, o)
+            ev[2].record(stream)
+            for j, (p, o) in enumerate(zip(pats, opts)):    # a5..a10 (Alg. 3 + reductions)
+                ev[3 + 2 * j].record(stream)
+                agis.sample_device(g, p, o, 0, ntiles, outs[j].data_ptr())
+                ev[4 + 2 * j].record(stream)
+            words = [o.cpu().numpy().view(np.uint64) for o in outs]   # step result to host
+            stream.synchronize()
+            res = []
+            for w in words:
+                h, sec, sx, sx2 = agis.tile_sums(w)
+                res.append((int(h.sum()), int(sec.sum()), float(sx.sum()), float(sx2.sum())))
+            t = {"preprocess": ev[0].elapsed_time(ev[1]), "tables": ev[1].elapsed_time(ev[2]),
+                 "sample": [ev[3 + 2 * j].elapsed_time(ev[4 + 2 * j]) for j in range(len(names))]}
+            if record is not None:
+                record.append((t, res))
+            return t, res
+
+        for _ in range(args.warmup):
+            step(None)
+        stream.synchronize()
+        barrier(world)
+        torch.cuda.synchronize()
+        clocks = ClockSampler(local)
+        clocks.start()
+        launches0 = agis.kernel_launches()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        recs = []
+        e0.record(stream)
+        for _ in range(args.steps):
+            step(recs)
+        e1.record(stream)
+        stream.synchronize()
+        torch.cuda.synchronize()
+        barrier(world)
+        launches = agis.kernel_launches() - launches0
+        clk = clocks.stop()
+        ms = e0.elapsed_time(e1) / args.steps
+        ms = allreduce_max(ms, world)
+        trials_per_step = trials * len(names)
+        value = trials_per_step * world / (ms / 1000.0)
+
+        # roofline of the sampler kernel: algorithmic sectors / its own event time
+        samp_ms = [sum(t["sample"]) for t, _ in recs]
+        sectors = [sum(r[1] for r in res) for _, res in recs]
+        per_launch_ms = statistics.mean([x for t, _ in recs for x in t["sample"]])
+        achieved = statistics.mean([s * 32 / (m / 1000.0) for s, m in zip(sectors, samp_ms)]) / 1e9
+        peak, peak_kind = measured_peaks()
+        traffic = profile_traffic(trials)
+        last = recs[-1][1]
+        phases = {k: statistics.mean([t[k] for t, _ in recs]) for k in ("preprocess", "tables")}
+        phases["sample"] = statistics.mean(samp_ms)
+        per_pattern = {n: {"estimate": r[2] / trials, "hits": r[0], "sectors_per_trial": r[1] / trials,
+                           "ms": statistics.mean([t["sample"][j] for t, _ in recs])}
+                       for j, (n, r) in enumerate(zip(names, last))}
+
+        # ---- end to end through the C ABI from pinned host buffers
+        e2e = None
+        if not args.no_e2e:
+            h_off = torch.from_numpy(off).pin_memory().numpy()
+            h_cols = torch.from_numpy(cols).pin_memory().numpy()
+            reps = max(1, min(args.steps, 2))
+            d2h = 0
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                ge = agis.Graph(ctx, h_off, h_cols, validate=False)
+                ge.preprocess(1, CMIN)
+                for p, o in zip(pats, opts):
+                    r = agis.estimate(ge, p, o)
+                    d2h += ntiles * 32 + 136
+                ge.close()
+            torch.cuda.synchronize()
+            dt = (time.perf_counter() - t0) / reps
+            e2e = {"value": trials_per_step / dt, "unit": "samples/s",
+                   "h2d_bytes_per_step": int(h_off.nbytes + h_cols.nbytes + len(names) * 600),
+                   "d2h_bytes_per_step": int(d2h / reps), "s_per_step": dt}
+
+        # ---- time to +-1% (95% CI): plain, batched, served; and f_uniform for contrast
+        tte = None
+        if not args.no_tte:
+            tte = {}
+            acc = dict(eps=0.01, delta=0.05, chunk_trials=1 << 16, min_trials=1 << 16)
+            plain = []
+            t0 = time.perf_counter()
+            for i, p in enumerate(pats):
+                o = agis.default_opts(mode=0, seed=101 + i, max_trials=1 << 34, **acc)
+                t1 = time.perf_counter()
+                r = agis.estimate(g, p, o)
+                plain.append({"pattern": names[i], "s": time.perf_counter() - t1, "trials": r["trials"],
+                              "converged": r["converged"], "estimate": r["estimate"]})
+            tte["plain_total_s"] = time.perf_counter() - t0
+            tte["plain"] = plain
+            bo = [agis.default_opts(mode=0, seed=101 + i, max_trials=1 << 34, **acc) for i in range(len(pats))]
+            t0 = time.perf_counter()
+            br = agis.estimate_batch(g, pats, bo)
+            tte["batched_total_s"] = time.perf_counter() - t0
+            tte["batched_same_result"] = all(a["trials"] == b["trials"] and a["estimate"] == b["estimate"]
+                                             for a, b in zip(plain, br))
+            srv = agis.Server(g, 200 << 30, 64)
+            t0 = time.perf_counter()
+            tickets = [srv.submit(p, o) for p, o in zip(pats, bo)]
+            done = {}
+            while len(done) < len(tickets):
+                for tk in tickets:
+                    if tk not in done:
+                        r = srv.poll(tk)
+                        if r is not None:
+                            done[tk] = r
+                time.sleep(0.0005)
+            tte["served_total_s"] = time.perf_counter() - t0
+            tte["served_same_result"] = all(done[tk]["trials"] == a["trials"] for tk, a in zip(tickets, plain))
+            srv.close()
+            uni = []
+            for i, p in enumerate(pats):
+                o = agis.default_opts(mode=2, seed=101 + i, max_trials=1 << 31, **acc)
+                t1 = time.perf_counter()
+                r = agis.estimate(g, p, o)
+                uni.append({"pattern": names[i], "s": time.perf_counter() - t1, "trials": r["trials"],
+                            "converged": r["converged"]})
+            tte["uniform_plain"] = uni
+
+    cpu = None
+    if pool is not None:
+        t_prep = pool.preprocess()
+        rate, n, dt, per = cpu_rate(pool, names, args.cpu_seconds)
+        cpu = {"value": rate, "unit": "samples/s", "cores": pool.procs, "kind": "oracle",
+               "sample": f"{per} trials of each of {', '.join(names)} (AUTO, seeds 1..4) on the same "
+                         f"scale-{args.scale} graph, split over {pool.procs} processes; {dt:.1f} s; "
+                         f"oracle preprocessing {t_prep:.1f} s not included"}
+        pool.close()
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"plain per-query launches: R-MAT scale {args.scale} (edge factor 16, "
+                               f"a=0.57 b=0.19 c=0.19), patterns {', '.join(names)}, 2^{args.log2_trials} "
+                               f"trials each, D^pi (beta 0.8), FP64 estimate and variance",
+                   "nv": info["nv"], "nnz": info["nnz"], "max_degree": info["max_degree"],
+                   "trials_per_pattern": trials, "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (CSR %.2f GB plus weight tables)" % ((off.nbytes + cols.nbytes) / 1e9),
+                   "graph_generation_s": t_gen},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "kernel": "sample_kernel",
+                     "peak_kind": peak_kind, "per_launch_ms": per_launch_ms,
+                     "algorithmic_bytes_per_launch": statistics.mean(sectors) * 32 / len(names)},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "phases_ms": phases,
+        "per_pattern": per_pattern,
+        "time_to_1pct": tte,
+    }
+    return line
+
+
+def run_reference(args, world, rank):
+    """The reference arm: the CPU oracle on the host cores, same metric and workload."""
+    if rank != 0:
+        return None
+    names = [n for n in args.patterns.split(",") if n]
+    off, cols, _ = make_workload(args.scale)
+    pool = OraclePool(off, cols)
+    t_prep = pool.preprocess()
+    rate, n, dt, per = cpu_rate(pool, names, max(2.0, args.cpu_seconds / 3))
+    times = []
+    for _ in range(args.warmup):
+        pool.sample(names, per)
+    for _ in range(args.steps):
+        nn, d = pool.sample(names, per)
+        times.append(d)
+    pool.close()
+    ms = 1000.0 * statistics.mean(times)
+    value = n / (ms / 1000.0)
+    cpu = {"value": value, "unit": "samples/s", "cores": pool.procs, "kind": "oracle",
+           "sample": f"{per} trials of each of {', '.join(names)} per step on the scale-{args.scale} graph "
+                     f"over {pool.procs} processes; oracle preprocessing {t_prep:.1f} s not included"}
+    return {"metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": f"plain per-query launches: R-MAT scale {args.scale}, patterns "
+                                   f"{', '.join(names)}, bounded sample of 2^{args.log2_trials} trials each",
+                       "parallelism": "host processes"},
+            "cpu_baseline": cpu,
+            "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse_args()
+    world, rank, local = dist_init()
+    if args.impl == "reference":
+        line = run_reference(args, world, rank)
+    else:
+        line = run_gpu(args, world, rank, local)
+    if rank == 0 and line is not None:
+        s = json.dumps(line)
+        print(s, flush=True)
+        if args.json_out:
+            with open(args.json_out, "w") as f:
+                f.write(s + "\n")
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,256 @@
+/*
+ * agis.h -- C ABI of the B300 (sm_103a) implementation of AGIS's approximate
+ * graph-pattern counting (Lee & Lee, "AGIS: Fast Approximate Graph Pattern Mining
+ * with Structure-Informed Sampling", PVLDB 19(2), arXiv 2601.01388).
+ *
+ * The problem (Sec. 2.1): given an undirected data graph G, a pattern P, an error
+ * bound eps and a confidence 1 - delta, return a (1 +- eps) estimate of C(G,P), the
+ * number of embeddings (injective maps V_P -> V_G that keep every pattern edge;
+ * automorphic copies are counted separately).  The estimate is the mean of
+ * independent sampler outputs of Alg. 3 (structure-informed neighbour sampling),
+ * each the inverse probability of its trajectory or 0, stopped by Alg. 1.
+ *
+ * Conventions for every call:
+ *   - The return value is an agis_status; nothing else signals errors, and no C++
+ *     exception or abort crosses this boundary.
+ *   - Handles (agis_ctx, agis_graph, agis_pattern, agis_server) are owned by the
+ *     library and released by the matching _destroy / _free call.
+ *   - Input arrays are copied before the call returns; output arrays are owned by
+ *     the caller and must hold the stated number of elements.
+ *   - "device" pointers are CUDA global-memory addresses of the context's device;
+ *     "host" pointers are ordinary (pageable or pinned) host memory.
+ *   - The graph is undirected and stored in CSR with both directions: int64 row
+ *     offsets off[nv+1] (off[0] = 0, non-decreasing) and int32 column ids
+ *     cols[nnz]; every row is sorted strictly ascending, has no self-loop, and every
+ *     entry (u, v) has its reverse (v, u) (Sec. 2: both graphs undirected).
+ *   - Patterns have 2..8 vertices, are connected (Alg. 2 grows the order along
+ *     edges) and have no self-loops or repeated edges.
+ *   - One agis_ctx may be used from one host thread at a time; an agis_server is
+ *     internally synchronised.
+ */
+#ifndef AGIS_H
+#define AGIS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    AGIS_OK = 0,
+    AGIS_ERR_ARG = -1,      /* a null handle/pointer or an out-of-range argument      */
+    AGIS_ERR_NOMEM = -2,    /* device or host allocation failed                         */
+    AGIS_ERR_CUDA = -3,     /* a CUDA runtime call failed (no device, launch error ...) */
+    AGIS_ERR_GRAPH = -4,    /* CSR violates the conventions above                       */
+    AGIS_ERR_PATTERN = -5,  /* pattern violates the conventions above                   */
+    AGIS_ERR_TIMEOUT = -6,  /* a bounded device loop hit its iteration cap              */
+    AGIS_ERR_BUSY = -7,     /* server: result not ready yet, or admission refused       */
+    AGIS_ERR_STATE = -8     /* call not valid in the handle's current state             */
+} agis_status;
+
+/* Distribution per step: AUTO = the decision function D^pi with threshold beta
+ * (Def. decision function); APPROX = f_approx at every step (beta = -inf in the
+ * Sec. 6 beta sweep); UNIFORM = f_uniform at every step (beta = +inf, which is
+ * ScaleGPM's NS-prune without symmetry breaking, Sec. 5.3). */
+typedef enum { AGIS_MODE_AUTO = 0, AGIS_MODE_APPROX = 1, AGIS_MODE_UNIFORM = 2 } agis_mode;
+
+typedef struct agis_ctx agis_ctx;
+typedef struct agis_graph agis_graph;
+typedef struct agis_pattern agis_pattern;
+typedef struct agis_server agis_server;
+
+/* Per-query options.  agis_default_opts fills eps = 0.1, delta = 0.01 (the paper's
+ * defaults, Sec. 6.1), beta = 0.8 (Def. decision function), mode AUTO, seed 1,
+ * chunk_trials = 65536, min_trials = 65536, max_trials = 2^32. */
+typedef struct {
+    double eps;             /* target relative error of Alg. 1                         */
+    double delta;           /* 1 - confidence; z = Phi^{-1}(1 - delta/2)               */
+    double beta;            /* decision threshold (AUTO mode)                          */
+    int32_t mode;           /* agis_mode                                               */
+    int32_t reserved;
+    uint64_t seed;          /* Philox key of this query's trials                       */
+    uint64_t min_trials;    /* Alg. 1 is not consulted before this many trials         */
+    uint64_t max_trials;    /* hard budget; with eps <= 0 exactly this many run        */
+    uint64_t chunk_trials;  /* checkpoint spacing for Alg. 1; multiple of 1024         */
+} agis_opts;
+
+typedef struct {
+    double estimate;        /* mean sampler output = estimate of C(G,P) (embeddings)    */
+    double subgraphs;       /* estimate / |Aut(P)|                                      */
+    double mean, var;       /* Alg. 1: mu and population sigma^2 of the outputs         */
+    double eps_hat;         /* Alg. 1 estimated relative error at the stopping point    */
+    double sum_x, sum_x2;   /* FP64 sums over the trials used                           */
+    uint64_t trials;        /* trials used (a multiple of chunk_trials unless capped)   */
+    uint64_t hits;          /* successful trajectories among them                       */
+    uint64_t sectors;       /* algorithmic 32-byte sectors of those trials (model)      */
+    int32_t converged;      /* 1 if Alg. 1 accepted eps at a checkpoint                 */
+    int32_t launches;       /* sampler kernel launches used                             */
+    double t_prep_s;        /* weight-table builds done for this call                  */
+    double t_sample_s;      /* wall time of the sampling loop                           */
+} agis_result;
+
+const char *agis_status_str(int status);
+void agis_default_opts(agis_opts *opts);
+
+/* ---- context -------------------------------------------------------------
+ * agis_create: binds CUDA device `device` and the CUDA stream `cuda_stream`
+ * (a cudaStream_t; NULL = the library's own non-blocking stream).  Every kernel
+ * of this context runs on that stream.  Errors: ARG (out is NULL), CUDA. */
+int agis_create(int device, void *cuda_stream, agis_ctx **out);
+int agis_destroy(agis_ctx *ctx);
+
+/* ---- graph ---------------------------------------------------------------
+ * agis_graph_load_csr: copies a CSR graph to the device (Sec. 5.4 "the graph is
+ * read and loaded in CSR format").  offsets: nv+1 entries, int64 if
+ * offsets_are_64bit else int32; cols: nnz int32 entries.  on_device = 1 means both
+ * pointers are device addresses of ctx's device, 0 means host memory.  validate = 1
+ * checks the CSR conventions on the device and returns GRAPH on a violation.
+ * The graph keeps a reference to ctx; free the graph before the ctx.
+ * Errors: ARG, NOMEM, CUDA, GRAPH. */
+int agis_graph_load_csr(agis_ctx *ctx, const void *offsets, int offsets_are_64bit,
+                        const int32_t *cols, int64_t nv, int64_t nnz, int on_device,
+                        int validate, agis_graph **out);
+
+/* agis_graph_preprocess: Sec. 4.4 -- for every vertex v the neighbour-degree sum
+ * nsum(v) = sum_{x in N(v)} d(x) (numerator of the average neighbour degree) and the
+ * sampled clustering coefficient C_v = max(c_min, hits(v)/d(v)) from d(v) probes of
+ * uniform ordered distinct neighbour pairs, probe j of v keyed by Philox4x64-10
+ * counter (v, j, 2, 0) and key (seed, 0); d(v) < 2 gives c_min.  Must precede any
+ * estimate; calling it again with new values drops cached weight tables.
+ * Errors: ARG (c_min outside (0, 1]), NOMEM, CUDA. */
+int agis_graph_preprocess(agis_graph *g, uint64_t seed, double c_min);
+
+/* agis_graph_info: nv, nnz (directed entries), max degree, device bytes held. */
+int agis_graph_info(const agis_graph *g, int64_t *nv, int64_t *nnz, int64_t *max_degree,
+                    uint64_t *device_bytes);
+
+/* agis_graph_stats_copy: copies nsum (uint64[nv]) and hits (uint32[nv]) of the last
+ * preprocess to caller-owned host arrays (either may be NULL).  Errors: ARG, STATE. */
+int agis_graph_stats_copy(const agis_graph *g, uint64_t *nsum, uint32_t *hits);
+
+/* agis_graph_weight_table: builds (or reuses) the quantised f_approx weight table
+ * of step configuration cfg = (|B|, |F1|, |I_eff|, |F2|) (Eq. probability_function)
+ * and copies it out: q[nv] uint64 weights, prefix[nv] uint64 inclusive running sums
+ * over v (either may be NULL), *shift = the power-of-two scale applied before
+ * flooring.  Used to check the tables bit for bit.  Errors: ARG, STATE, NOMEM, CUDA. */
+int agis_graph_weight_table(agis_graph *g, const int32_t cfg[4], uint64_t *q,
+                            uint64_t *prefix, int32_t *shift);
+
+/* agis_graph_row_prefix: copies the per-row inclusive running sums of q over each
+ * row's neighbours for configuration cfg (nnz uint64, caller-owned host array). */
+int agis_graph_row_prefix(agis_graph *g, const int32_t cfg[4], uint64_t *row_prefix);
+
+/* agis_graph_validate: re-checks the CSR conventions above on the device (e.g. for a
+ * generated graph).  Returns OK or GRAPH. */
+int agis_graph_validate(agis_graph *g);
+
+/* agis_graph_copy_csr: copies the device CSR to caller-owned host arrays off[nv+1]
+ * (int64) and cols[nnz] (int32); either may be NULL. */
+int agis_graph_copy_csr(const agis_graph *g, int64_t *off, int32_t *cols);
+
+/* agis_graph_drop_tables: frees every cached weight table (they are rebuilt on
+ * demand). */
+int agis_graph_drop_tables(agis_graph *g);
+int agis_graph_free(agis_graph *g);
+
+/* ---- synthetic graphs on the device ---------------------------------------
+ * agis_graph_generate_rmat: R-MAT (Chakrabarti et al., SDM'04) with 2^scale
+ * vertices and edge_factor * 2^scale edge draws, quadrant probabilities (a, b, c,
+ * 1-a-b-c), symmetrised, self-loops and duplicates removed, ids permuted by a
+ * seeded bijection; built on the device in chunks.  Errors: ARG, NOMEM, CUDA. */
+int agis_graph_generate_rmat(agis_ctx *ctx, int scale, int edge_factor, double a, double b,
+                             double c, uint64_t seed, agis_graph **out);
+
+/* ---- pattern -------------------------------------------------------------
+ * agis_pattern_create: k vertices (2..8), ne undirected edges as pairs
+ * edge_pairs[2*ne] (host).  Computes the matching order pi (Alg. 2, ties to the
+ * smallest id), the auxiliary arrays B, F1, I_eff, F2 per step (Def. auxiliary
+ * arrays), Certainty per step (Def. decision function, E^{>=2hop} over E_P) and
+ * |Aut(P)|.  Errors: ARG, PATTERN. */
+int agis_pattern_create(int k, int ne, const int32_t *edge_pairs, agis_pattern **out);
+
+/* agis_pattern_info: order[8] (pattern vertex of step i), cfg[8][4] = (|B|, |F1|,
+ * |I_eff|, |F2|) per step, certainty[8], back[8] = bitmask over earlier steps of the
+ * backward neighbours, *automorphisms = |Aut(P)|.  Entries past k are zero.  Any
+ * output pointer may be NULL. */
+int agis_pattern_info(const agis_pattern *p, int32_t *k, int32_t order[8], int32_t cfg[8][4],
+                      double certainty[8], uint8_t back[8], uint64_t *automorphisms);
+
+/* agis_pattern_decide: D^pi per step for (mode, beta) into use_approx[8]. */
+int agis_pattern_decide(const agis_pattern *p, int32_t mode, double beta, uint8_t use_approx[8]);
+int agis_pattern_free(agis_pattern *p);
+
+/* ---- estimation ------------------------------------------------------------
+ * agis_estimate: one query, plain per-query launches.  Runs Alg. 3 trials
+ * 0, 1, 2, ... (trial t draws step i from Philox4x64-10 counter (t, i, 1, 0), key
+ * (seed, 0)) in tiles of 1024 on the device, and evaluates Alg. 1 on host at every
+ * chunk_trials checkpoint once min_trials trials are in.  The result is that of the
+ * first converged checkpoint, or of max_trials; it is a deterministic function of
+ * (graph, pattern, opts).  eps <= 0 runs exactly max_trials (rounded up to 1024).
+ * Errors: ARG, STATE (graph not preprocessed), NOMEM, CUDA, TIMEOUT. */
+int agis_estimate(agis_graph *g, const agis_pattern *p, const agis_opts *opts,
+                  agis_result *out);
+
+/* agis_estimate_batch: n queries (patterns[i], opts[i]) in one persistent,
+ * work-stealing launch per epoch, replayed from a captured CUDA graph; tiles of
+ * all unconverged queries share each launch.  Each out[i] equals what
+ * agis_estimate(g, patterns[i], &opts[i]) returns.  Errors: as agis_estimate. */
+int agis_estimate_batch(agis_graph *g, int n, const agis_pattern *const *patterns,
+                        const agis_opts *opts, agis_result *out);
+
+/* agis_dump_trials: per-trial record of trials [first, first+count) of the query:
+ * emb[count*8] int32 trajectory (step order; -1 after a failed step), hit[count]
+ * (1 = the trajectory is an embedding), x[count] FP64 sampler output (Alg. 3:
+ * 1/p or 0), sectors[count] algorithmic sectors.  Host arrays; any may be NULL.
+ * Errors: ARG, STATE, NOMEM, CUDA. */
+int agis_dump_trials(agis_graph *g, const agis_pattern *p, const agis_opts *opts,
+                     uint64_t first, uint64_t count, int32_t *emb, uint8_t *hit, double *x,
+                     uint64_t *sectors);
+
+/* agis_sample_device: fixed-budget sampling with all buffers on the device:
+ * trials [first, first + ntiles*1024) of the query, per-tile sums written to
+ * tile_out (device, ntiles * 4 uint64 words per tile: hits, sectors, then the FP64
+ * sum X and sum X^2 bit patterns).  Enqueued on ctx's stream, no host sync.
+ * Errors: ARG, STATE, NOMEM, CUDA. */
+int agis_sample_device(agis_graph *g, const agis_pattern *p, const agis_opts *opts,
+                       uint64_t first, uint64_t ntiles, uint64_t *tile_out);
+
+/* agis_prepare: builds, for the query's f_approx steps, the quantised weight tables
+ * of Eq. probability_function and their prefix sums (Sec. 4.4 / Sec. 5.1: f_approx
+ * needs the per-vertex weights of every candidate); later calls reuse them.  Blocks
+ * until the tables are ready.  Errors: ARG, STATE, NOMEM, CUDA. */
+int agis_prepare(agis_graph *g, const agis_pattern *p, const agis_opts *opts);
+
+/* agis_kernel_launches: number of this library's CUDA kernel launches so far in
+ * the process (all contexts); a diagnostic for counting device work. */
+uint64_t agis_kernel_launches(void);
+
+/* agis_z_of_delta: Phi^{-1}(1 - delta/2) as Alg. 1 uses it. */
+double agis_z_of_delta(double delta);
+
+/* ---- serving -------------------------------------------------------------
+ * A server keeps the graph resident and runs a scheduler thread that admits
+ * queries while a slot is free and their weight tables fit in scratch_bytes of
+ * device memory, runs all admitted queries together in epochs (each epoch one
+ * persistent launch over every admitted query's next tiles), retires queries at
+ * their first converged checkpoint and admits waiting ones between epochs
+ * (continuous batching).  Results equal agis_estimate's. */
+int agis_server_create(agis_graph *g, size_t scratch_bytes, int max_slots, agis_server **out);
+/* agis_server_submit: copies the pattern and options; *ticket identifies the query.
+ * Errors: ARG, BUSY (more than 65536 queries waiting). */
+int agis_server_submit(agis_server *s, const agis_pattern *p, const agis_opts *opts,
+                       uint64_t *ticket);
+/* agis_server_poll: AGIS_OK and *out filled when done (the ticket is then
+ * released), AGIS_ERR_BUSY while queued or running, ARG for an unknown ticket, or
+ * the query's own error status.  latency_s (may be NULL) = completion - submit. */
+int agis_server_poll(agis_server *s, uint64_t ticket, agis_result *out, double *latency_s);
+/* agis_server_stats: queries completed, epochs launched, peak admitted slots. */
+int agis_server_stats(agis_server *s, uint64_t *completed, uint64_t *epochs, int32_t *peak_slots);
+int agis_server_destroy(agis_server *s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AGIS_H */

@@ -291,10 +291,11 @@ void orc_cc_pair(uint64_t d, uint64_t r, uint64_t *a, uint64_t *b)
 /* nsum[v] = sum of d(x) over x in N(v)  (numerator of the average neighbour degree);
  * hits[v] = number of the d(v) sampled neighbour pairs that are joined by an edge
  * (the sampled clustering coefficient, Sec. 4.4). */
-void orc_graph_stats(int64_t nv, const int64_t *off, const int32_t *cols, uint64_t seed,
-                     uint64_t *nsum, uint32_t *hits)
+void orc_graph_stats_range(int64_t nv, const int64_t *off, const int32_t *cols, uint64_t seed,
+                           int64_t v0, int64_t v1, uint64_t *nsum, uint32_t *hits)
 {
-    for (int64_t v = 0; v < nv; ++v) {
+    (void)nv;
+    for (int64_t v = v0; v < v1; ++v) {
         int64_t d = off[v + 1] - off[v];
         uint64_t s = 0;
         for (int64_t e = off[v]; e < off[v + 1]; ++e) {
@@ -314,6 +315,12 @@ void orc_graph_stats(int64_t nv, const int64_t *off, const int32_t *cols, uint64
         }
         hits[v] = h;
     }
+}
+
+void orc_graph_stats(int64_t nv, const int64_t *off, const int32_t *cols, uint64_t seed,
+                     uint64_t *nsum, uint32_t *hits)
+{
+    orc_graph_stats_range(nv, off, cols, seed, 0, nv, nsum, hits);
 }
 
 /* Eq. probability_function: T[F1] * T[I1] * T[F2] with
@@ -370,6 +377,19 @@ uint64_t orc_quantise(double w, int64_t d, int32_t b, int32_t f1, int32_t shift)
     double s = ldexp(w, shift);
     uint64_t q = (uint64_t)floor(s);
     return q < 1 ? 1 : q;
+}
+
+/* Whole quantised table of one configuration: q[v] for every vertex and the shift
+ * used (a plain loop over orc_weight / orc_quantise). */
+int32_t orc_weight_table(int64_t nv, const int64_t *off, const uint64_t *nsum, const uint32_t *hits,
+                         double c_min, int32_t b, int32_t f1, int32_t ie, int32_t f2, uint64_t *q)
+{
+    int32_t shift = orc_quant_shift(nv, off, nsum, hits, c_min, b, f1, ie, f2);
+    for (int64_t v = 0; v < nv; ++v) {
+        int64_t d = off[v + 1] - off[v];
+        q[v] = orc_quantise(orc_weight(d, nsum[v], hits[v], c_min, b, f1, ie, f2), d, b, f1, shift);
+    }
+    return shift;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -498,9 +518,9 @@ static int64_t build_candidates(const orc_query *Q, int i, const int32_t *tau, u
  *   later : one sector per backward vertex's offsets; one backward edge: i-1
  *           trajectory-membership searches in the row, a running-weight search in
  *           the row under f_approx (+1 for q(v)), one sector for the chosen entry;
- *           several: a scan of the shortest backward row, one membership search per
- *           scanned entry per other backward row, one q gather per candidate under
- *           f_approx. */
+ *           several: a scan of the shortest backward row; for each other backward
+ *           row the cheaper of reading it once (a merge) and one membership search
+ *           per scanned entry; one q gather per candidate under f_approx. */
 static uint64_t step_sectors(const orc_query *Q, int i, const int32_t *tau, int64_t nS)
 {
     const orc_plan *p = &Q->plan;
@@ -525,7 +545,10 @@ static uint64_t step_sectors(const orc_query *Q, int i, const int32_t *tau, int6
     for (int b = 0; b < nb; ++b) {
         if (b == a) continue;
         int32_t v = tau[p->back[i][b]];
-        s += (uint64_t)da * sec_search(Q->off[v + 1] - Q->off[v], 4);
+        int64_t m = Q->off[v + 1] - Q->off[v];
+        uint64_t read_once = (uint64_t)((4 * (m > 0 ? m : 1) + 31) / 32);
+        uint64_t search_each = (uint64_t)da * sec_search(m, 4);
+        s += read_once < search_each ? read_once : search_each;
     }
     if (Q->use_approx[i]) s += (uint64_t)nS;
     return s;

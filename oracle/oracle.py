@@ -61,6 +61,8 @@ def lib():
         L.orc_cc_pair.argtypes = [C.c_uint64, C.c_uint64, P(C.c_uint64), P(C.c_uint64)]
         L.orc_graph_stats.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_uint64,
                                       C.c_void_p, C.c_void_p]
+        L.orc_graph_stats_range.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_uint64,
+                                            C.c_int64, C.c_int64, C.c_void_p, C.c_void_p]
         L.orc_weight.argtypes = [C.c_int64, C.c_uint64, C.c_uint32, C.c_double,
                                  C.c_int32, C.c_int32, C.c_int32, C.c_int32]
         L.orc_weight.restype = C.c_double
@@ -69,6 +71,9 @@ def lib():
         L.orc_quant_shift.restype = C.c_int32
         L.orc_quantise.argtypes = [C.c_double, C.c_int64, C.c_int32, C.c_int32, C.c_int32]
         L.orc_quantise.restype = C.c_uint64
+        L.orc_weight_table.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double,
+                                       C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_void_p]
+        L.orc_weight_table.restype = C.c_int32
         L.orc_query_create.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                        C.c_double, C.c_int32, C.c_int32, P(C.c_int32),
                                        C.c_int32, C.c_double, C.c_uint64]
@@ -161,6 +166,11 @@ def graph_stats(off, cols, seed=1):
     return nsum, hits
 
 
+def graph_stats_range(off, cols, seed, v0, v1, nsum, hits):
+    """Fills nsum[v0:v1], hits[v0:v1] in place (arrays of length nv)."""
+    lib().orc_graph_stats_range(len(off) - 1, _ptr(off), _ptr(cols), seed, v0, v1, _ptr(nsum), _ptr(hits))
+
+
 def weight(d, nsum, hits, c_min, cfg):
     b, f1, ie, f2 = cfg
     return float(lib().orc_weight(d, nsum, hits, c_min, b, f1, ie, f2))
@@ -174,6 +184,15 @@ def quant_shift(off, nsum, hits, c_min, cfg):
 def quantise(w, d, cfg, shift):
     b, f1, _, _ = cfg
     return int(lib().orc_quantise(w, d, b, f1, shift))
+
+
+def weight_table(off, nsum, hits, c_min, cfg):
+    off = np.ascontiguousarray(off, dtype=np.int64)
+    nsum = np.ascontiguousarray(nsum, dtype=np.uint64)
+    hits = np.ascontiguousarray(hits, dtype=np.uint32)
+    q = np.zeros(len(off) - 1, dtype=np.uint64)
+    sh = lib().orc_weight_table(len(off) - 1, _ptr(off), _ptr(nsum), _ptr(hits), c_min, *cfg, _ptr(q))
+    return q, int(sh)
 
 
 def z_of_delta(delta):

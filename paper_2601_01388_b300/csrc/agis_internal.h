@@ -1,0 +1,216 @@
+// Internal types shared by the library's translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/agis.h"
+
+namespace agis {
+
+constexpr int kMaxK = 8;
+constexpr int kTile = 1024;          // trials per work item (one CTA at a time)
+constexpr int kBlock = 256;          // threads per CTA of the sampler
+constexpr int kWarps = kBlock / 32;
+constexpr uint64_t kStreamTrial = 1; // Philox counter word 2 of a trial draw
+constexpr uint64_t kStreamCC = 2;    // ... of a clustering-coefficient probe
+
+// One step of a compiled query as the sampler kernel reads it.
+struct DevStep {
+    int32_t nb;                 // |B[i]|: number of backward neighbours
+    int16_t approx;             // D(i): 1 = f_approx, 0 = f_uniform
+    int16_t inc;                // backward set = previous step's plus the previous vertex
+    int8_t back[kMaxK];         // step indices of the backward neighbours
+    const uint64_t *q;          // quantised f_approx weight per vertex (approx only)
+    const uint64_t *pref;       // step 0: inclusive prefix over vertices; |B| = 1: row prefix
+};
+
+struct DevQuery {
+    int32_t k;
+    int32_t pad;
+    uint64_t seed;
+    uint64_t W1;                // total step-1 weight (f_approx sum or nnz)
+    DevStep step[kMaxK];
+};
+
+// A work item: `count` trials of query `query` starting at trial `first`; the tile
+// sums go to out[4*slot .. 4*slot+3] (hits, sectors, bits of sum X, bits of sum X^2).
+struct WorkItem {
+    uint32_t query;
+    uint32_t count;
+    uint64_t first;
+    uint64_t slot;
+};
+
+// Where a dump launch writes per-trial records (index = trial - dump_first).
+struct DumpView {
+    int32_t *emb;
+    uint8_t *hit;
+    double *x;
+    uint64_t *sectors;
+    uint64_t first;
+};
+
+struct GraphView {
+    const int64_t *off;
+    const int32_t *cols;
+    int64_t nv;
+    int64_t nnz;
+};
+
+struct WeightTable {
+    int32_t cfg[4];
+    int32_t shift = 0;
+    uint64_t *q = nullptr;      // nv
+    uint64_t *pref = nullptr;   // nv, inclusive prefix over vertices (|B| = 0 configs)
+    uint64_t *rowp = nullptr;   // nnz, inclusive prefix inside each row (|B| = 1 configs)
+    uint64_t total = 0;
+    size_t bytes = 0;
+    uint64_t last_use = 0;
+    int pins = 0;               // queries of a running server that use it
+};
+
+// Launch-side scratch: device buffers grown on demand and reused across launches.
+struct LaunchBuffers {
+    DevQuery *d_queries = nullptr;
+    size_t cap_queries = 0;
+    WorkItem *d_items = nullptr;
+    size_t cap_items = 0;
+    uint64_t *d_out = nullptr;  // 4 words per item slot
+    size_t cap_out = 0;
+    uint32_t *d_counter = nullptr; // [0] work counter, [1] number of items
+    void *d_scratch = nullptr;     // per-warp candidate lists of the sampler
+    size_t scratch_bytes = 0;
+    uint32_t scratch_cap = 0;      // entries per list
+    int scratch_grid = 0;          // CTAs the scratch was sized for
+    // pinned host mirrors
+    DevQuery *h_queries = nullptr;
+    WorkItem *h_items = nullptr;
+    uint64_t *h_out = nullptr;
+    uint32_t *h_counter = nullptr;
+    size_t hcap_queries = 0, hcap_items = 0, hcap_out = 0;
+    // captured epoch graph
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphNode_t n_h2d_q = nullptr, n_h2d_i = nullptr, n_h2d_c = nullptr, n_kernel = nullptr,
+                    n_d2h = nullptr;
+    int graph_grid = 0;
+    uint64_t generation = 0;       // bumps when device buffers move (graph must be rebuilt)
+    uint64_t graph_generation = ~0ull;
+};
+
+}  // namespace agis
+
+struct agis_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int sm_count = 0;
+    int blocks_per_sm = 0;      // sampler CTAs per SM chosen by the autotuner (0 = not tuned)
+};
+
+struct agis_pattern {
+    int k = 0;
+    int order[agis::kMaxK] = {0};
+    int nback[agis::kMaxK] = {0};
+    int back[agis::kMaxK][agis::kMaxK] = {{0}};
+    int cfg[agis::kMaxK][4] = {{0}};
+    double certainty[agis::kMaxK] = {0};
+    uint64_t aut = 0;
+};
+
+struct agis_graph {
+    agis_ctx *ctx = nullptr;
+    int64_t nv = 0, nnz = 0, max_deg = 0;
+    int64_t *off = nullptr;
+    int32_t *cols = nullptr;
+    uint64_t *nsum = nullptr;
+    uint32_t *hits = nullptr;
+    bool prepped = false;
+    double c_min = 0.0;
+    uint64_t prep_seed = 0;
+    std::map<uint64_t, agis::WeightTable> tables;
+    uint64_t use_clock = 0;
+    std::recursive_mutex mu;
+    agis::LaunchBuffers lb;     // used by estimate/batch/dump (under mu)
+    size_t rowp_budget = 0;     // largest row-prefix table built (bytes); beyond it draws scan rows
+};
+
+namespace agis {
+
+// graph.cu
+int build_weight_table(agis_graph *g, const int32_t cfg[4], bool need_pref, bool need_rowp,
+                       WeightTable **out);
+uint64_t cfg_key(const int32_t cfg[4]);
+size_t table_bytes(const agis_graph *g, const int32_t cfg[4], bool need_pref, bool need_rowp);
+void free_table(WeightTable &t);
+
+// sample.cu
+int launch_sampler(agis_graph *g, LaunchBuffers &lb, int grid, const DumpView *dump,
+                   cudaStream_t stream, uint64_t implicit_first, uint64_t implicit_count,
+                   uint64_t *tile_out);
+int add_sampler_node(agis_graph *g, LaunchBuffers &lb, int grid, cudaGraph_t graph,
+                     const cudaGraphNode_t *deps, size_t ndeps, cudaGraphNode_t *node);
+int sampler_occupancy(int *blocks_per_sm);
+
+// runtime.cu
+int make_dev_query(agis_graph *g, const agis_pattern *p, const agis_opts *o, DevQuery *dq,
+                   double *t_prep);
+int ensure_buffers(LaunchBuffers &lb, size_t n_queries, size_t n_items);
+int grid_for(agis_graph *g, size_t n_items);
+int ensure_scratch(agis_graph *g, LaunchBuffers &lb, int grid);
+size_t scratch_stride(uint32_t cap);
+
+// Per-query progress of the adaptive loop (Alg. 1 at chunk checkpoints).
+struct QueryRun {
+    const agis_pattern *p = nullptr;
+    agis_opts o{};
+    DevQuery dq{};
+    double z = 0.0;
+    uint64_t max_tiles = 0;       // ceil(max_trials / 1024)
+    uint64_t tiles_per_chunk = 0;
+    uint64_t done_tiles = 0;      // tiles whose sums are in
+    uint64_t trials_done = 0;
+    uint64_t hits = 0, sectors = 0;
+    double sx = 0.0, sx2 = 0.0;
+    uint64_t ck_trials = 0, ck_hits = 0, ck_sectors = 0;   // at the last checkpoint
+    double ck_sx = 0.0, ck_sx2 = 0.0;
+    bool finished = false;
+    bool converged = false;
+    int launches = 0;
+    double t_prep = 0.0;
+};
+int check_opts(const agis_opts *o);
+int init_run(agis_graph *g, const agis_pattern *p, const agis_opts *o, QueryRun &r);
+uint64_t next_tiles(const QueryRun &r);
+void absorb(QueryRun &r, const uint64_t *tiles, uint64_t n);
+void fill_result(const QueryRun &r, agis_result *out);
+int run_epoch_graph(agis_graph *g, std::vector<QueryRun *> &runs, const std::vector<uint64_t> &ntiles,
+                    size_t total);
+double now_s();
+
+inline int cuda_status(cudaError_t e) { return e == cudaSuccess ? AGIS_OK : AGIS_ERR_CUDA; }
+
+// process-wide count of kernel launches (diagnostics)
+extern std::atomic<uint64_t> g_launches;
+inline void count_launch(uint64_t n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+}  // namespace agis
+
+#define AGIS_CUDA_TRY(expr)                                   \
+    do {                                                      \
+        cudaError_t _e = (expr);                              \
+        if (_e != cudaSuccess) {                              \
+            return _e == cudaErrorMemoryAllocation ? AGIS_ERR_NOMEM : AGIS_ERR_CUDA; \
+        }                                                     \
+    } while (0)

@@ -1,0 +1,603 @@
+// Device graph: CSR ingest and validation, Sec. 4.4 preprocessing (neighbour-degree
+// sums and sampled clustering coefficients), and the per-step-configuration weight
+// tables of Eq. probability_function with their prefix sums.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "agis_internal.h"
+#include "philox.cuh"
+
+namespace agis {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ int64_t row_find(const int32_t *row, int64_t d, int32_t x)
+{
+    // last position with row[pos] <= x; the number of probes depends on d only
+    if (d <= 0) return -1;
+    int64_t lo = 0, len = d;
+    while (len > 1) {
+        const int64_t half = len >> 1;
+        if (__ldg(row + lo + half) <= x) lo += half;
+        len -= half;
+    }
+    return __ldg(row + lo) == x ? lo : -1;
+}
+
+// ---------------------------------------------------------------- validation
+
+__global__ void k_check_offsets(const int64_t *off, int64_t nv, int64_t nnz, int *err)
+{
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v <= nv;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t o = off[v];
+        bool bad = (v == 0 && o != 0) || (v == nv && o != nnz) || o < 0 || o > nnz;
+        if (v < nv && off[v + 1] < o) bad = true;
+        if (bad) atomicOr(err, 1);
+    }
+}
+
+// one warp per row: range, self-loop, strict order and presence of the reverse entry
+__global__ void k_check_rows(const int64_t *off, const int32_t *cols, int64_t nv, int *err)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t v = warp; v < nv; v += nwarps) {
+        const int64_t s = off[v], e = off[v + 1];
+        for (int64_t i = s + lane; i < e; i += 32) {
+            const int32_t x = cols[i];
+            bool bad = x < 0 || x >= nv || x == v || (i > s && cols[i - 1] >= x);
+            if (!bad) bad = row_find(cols + off[x], off[x + 1] - off[x], (int32_t)v) < 0;
+            if (bad) atomicOr(err, 2);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- Sec. 4.4
+
+// nsum(v) = sum of d(x) over the neighbours x of v; one warp per vertex
+__global__ void k_neighbour_degree_sum(const int64_t *off, const int32_t *cols, int64_t nv,
+                                       uint64_t *nsum)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t v = warp; v < nv; v += nwarps) {
+        const int64_t s = off[v], e = off[v + 1];
+        uint64_t acc = 0;
+        for (int64_t i = s + lane; i < e; i += 32) {
+            const int32_t x = __ldg(cols + i);
+            acc += (uint64_t)(__ldg(off + x + 1) - __ldg(off + x));
+        }
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+        if (lane == 0) nsum[v] = acc;
+    }
+}
+
+// hits(v): probe j of v draws r in [0, d(d-1)), names the ordered distinct pair
+// a = r / (d-1), b = r mod (d-1) (+1 if >= a) of row positions, and hits when the
+// two neighbours are adjacent.  One warp per vertex, lanes over probes.
+__global__ void k_cluster_hits(const int64_t *off, const int32_t *cols, int64_t nv, uint64_t seed,
+                               uint32_t *hits)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t v = warp; v < nv; v += nwarps) {
+        const int64_t s = off[v];
+        const int64_t d = off[v + 1] - s;
+        uint32_t h = 0;
+        if (d >= 2) {
+            const uint64_t dm1 = (uint64_t)(d - 1);
+            for (int64_t j = lane; j < d; j += 32) {
+                const uint64_t r = draw_below((uint64_t)d * dm1, (uint64_t)v, (uint64_t)j, kStreamCC, seed);
+                const uint64_t a = r / dm1, bp = r - a * dm1;
+                const uint64_t b = bp + (bp >= a ? 1u : 0u);
+                const int32_t x = __ldg(cols + s + (int64_t)a), y = __ldg(cols + s + (int64_t)b);
+                h += row_find(cols + __ldg(off + x), __ldg(off + x + 1) - __ldg(off + x), y) >= 0;
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) h += __shfl_xor_sync(kFull, h, o);
+        if (lane == 0) hits[v] = h;
+    }
+}
+
+// ---------------------------------------------------------------- Eq. probability_function
+
+// T[F1] * T[I1] * T[F2] in IEEE double, round-to-nearest products and quotients in
+// the order written (binom by the multiplicative recurrence, powers by repeated
+// products), so that the host-side check reproduces every bit.
+__device__ __forceinline__ double step_weight(int64_t d, uint64_t nsum, uint32_t hits, double c_min,
+                                              int b, int f1, int ie, int f2)
+{
+    const int64_t n = d - b;
+    if (n < f1) return 0.0;
+    double t_f1 = 1.0;
+    for (int j = 0; j < f1; ++j) {
+        t_f1 = __dmul_rn(t_f1, (double)(n - j));
+        t_f1 = __ddiv_rn(t_f1, (double)(j + 1));
+    }
+    double cv = c_min;
+    if (d >= 2) {
+        cv = __ddiv_rn((double)hits, (double)d);
+        cv = cv < c_min ? c_min : cv;
+        cv = cv > 1.0 ? 1.0 : cv;
+    }
+    double t_i1 = 1.0;
+    for (int j = 0; j < ie; ++j) t_i1 = __dmul_rn(t_i1, cv);
+    double t_f2 = 1.0;
+    if (f2 > 0) {
+        const double avg = __ddiv_rn((double)nsum, (double)d);
+        for (int j = 0; j < f2; ++j) t_f2 = __dmul_rn(t_f2, avg);
+    }
+    return __dmul_rn(__dmul_rn(t_f1, t_i1), t_f2);
+}
+
+__global__ void k_weight_max(const int64_t *off, const uint64_t *nsum, const uint32_t *hits,
+                             int64_t nv, double c_min, int b, int f1, int ie, int f2,
+                             unsigned long long *wmax_bits)
+{
+    double m = 0.0;
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nv;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const double w = step_weight(off[v + 1] - off[v], nsum[v], hits[v], c_min, b, f1, ie, f2);
+        m = w > m ? w : m;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const double other = __shfl_xor_sync(kFull, m, o);
+        m = other > m ? other : m;
+    }
+    // non-negative doubles order like their bit patterns
+    if ((threadIdx.x & 31) == 0) atomicMax(wmax_bits, (unsigned long long)__double_as_longlong(m));
+}
+
+__global__ void k_weight_quantise(const int64_t *off, const uint64_t *nsum, const uint32_t *hits,
+                                  int64_t nv, double c_min, int b, int f1, int ie, int f2, int shift,
+                                  uint64_t *q)
+{
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nv;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t d = off[v + 1] - off[v];
+        uint64_t out = 0;
+        if (d - b >= f1) {
+            const double w = step_weight(d, nsum[v], hits[v], c_min, b, f1, ie, f2);
+            const double scaled = floor(ldexp(w, shift));
+            out = scaled < 1.0 ? 1u : (uint64_t)scaled;
+        }
+        q[v] = out;
+    }
+}
+
+// ---------------------------------------------------------------- prefix sums
+// Inclusive scan of uint64 over n entries in three passes (tile sums, scan of the
+// tile sums, tile-local scans plus carry).  Integer addition makes the result
+// independent of the order.
+
+constexpr int kScanThreads = 256, kScanPer = 8, kScanTile = kScanThreads * kScanPer;
+
+__device__ __forceinline__ uint64_t block_incl_scan(uint64_t v, uint64_t *warp_tot)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t n = __shfl_up_sync(kFull, v, o);
+        if (lane >= o) v += n;
+    }
+    if (lane == 31) warp_tot[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        uint64_t t = lane < kScanThreads / 32 ? warp_tot[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t n = __shfl_up_sync(kFull, t, o);
+            if (lane >= o) t += n;
+        }
+        if (lane < kScanThreads / 32) warp_tot[lane] = t;
+    }
+    __syncthreads();
+    const uint64_t before = w > 0 ? warp_tot[w - 1] : 0;
+    __syncthreads();
+    return v + before;
+}
+
+__global__ void k_scan_tile_sums(const uint64_t *in, int64_t n, uint64_t *tile_sums)
+{
+    __shared__ uint64_t wt[32];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanPer;
+    uint64_t s = 0;
+    for (int j = 0; j < kScanPer; ++j) if (base + j < n) s += in[base + j];
+    const uint64_t incl = block_incl_scan(s, wt);
+    if (threadIdx.x == kScanThreads - 1) tile_sums[blockIdx.x] = incl;
+}
+
+__global__ void k_scan_single(uint64_t *x, int64_t n)
+{
+    __shared__ uint64_t wt[32];
+    __shared__ uint64_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < n; base += kScanThreads) {
+        const int64_t i = base + threadIdx.x;
+        const uint64_t v = i < n ? x[i] : 0;
+        const uint64_t incl = block_incl_scan(v, wt);
+        const uint64_t c = carry;
+        if (i < n) x[i] = incl + c;
+        __syncthreads();
+        if (threadIdx.x == kScanThreads - 1) carry = c + incl;
+        __syncthreads();
+    }
+}
+
+__global__ void k_scan_apply(const uint64_t *in, int64_t n, const uint64_t *tile_incl, uint64_t *out)
+{
+    __shared__ uint64_t wt[32];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanPer;
+    uint64_t vals[kScanPer];
+    uint64_t s = 0;
+    for (int j = 0; j < kScanPer; ++j) {
+        vals[j] = base + j < n ? in[base + j] : 0;
+        s += vals[j];
+    }
+    const uint64_t incl = block_incl_scan(s, wt);
+    uint64_t run = incl - s + (blockIdx.x > 0 ? tile_incl[blockIdx.x - 1] : 0);
+    for (int j = 0; j < kScanPer; ++j) {
+        run += vals[j];
+        if (base + j < n) out[base + j] = run;
+    }
+}
+
+// Row prefix: for entry e of row v, sum of q(cols[e']) over e' in [off[v], e].
+// One warp per row, windows of 32 entries with a running carry.
+__global__ void k_row_prefix(const int64_t *off, const int32_t *cols, int64_t nv, const uint64_t *q,
+                             uint64_t *rowp)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t v = warp; v < nv; v += nwarps) {
+        const int64_t s = off[v], e = off[v + 1];
+        uint64_t carry = 0;
+        for (int64_t i0 = s; i0 < e; i0 += 32) {
+            const int64_t i = i0 + lane;
+            uint64_t w = i < e ? __ldg(q + __ldg(cols + i)) : 0;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint64_t n = __shfl_up_sync(kFull, w, o);
+                if (lane >= o) w += n;
+            }
+            if (i < e) rowp[i] = carry + w;
+            carry += __shfl_sync(kFull, w, 31);
+        }
+    }
+}
+
+int grid_stride_blocks(const agis_graph *g, int64_t work, int threads)
+{
+    int64_t blocks = (work + threads - 1) / threads;
+    const int64_t cap = (int64_t)g->ctx->sm_count * 16;
+    if (blocks > cap) blocks = cap;
+    return blocks < 1 ? 1 : (int)blocks;
+}
+
+int inclusive_scan(agis_graph *g, const uint64_t *in, int64_t n, uint64_t *out)
+{
+    cudaStream_t st = g->ctx->stream;
+    const int64_t tiles = (n + kScanTile - 1) / kScanTile;
+    if (tiles == 0) return AGIS_OK;
+    uint64_t *tile_sums = nullptr;
+    AGIS_CUDA_TRY(cudaMallocAsync(&tile_sums, sizeof(uint64_t) * tiles, st));
+    count_launch();
+    k_scan_tile_sums<<<(unsigned)tiles, kScanThreads, 0, st>>>(in, n, tile_sums);
+    count_launch();
+    k_scan_single<<<1, kScanThreads, 0, st>>>(tile_sums, tiles);
+    count_launch();
+    k_scan_apply<<<(unsigned)tiles, kScanThreads, 0, st>>>(in, n, tile_sums, out);
+    cudaError_t e = cudaGetLastError();
+    cudaFreeAsync(tile_sums, st);
+    return cuda_status(e);
+}
+
+}  // namespace
+
+uint64_t cfg_key(const int32_t cfg[4])
+{
+    return ((uint64_t)(uint8_t)cfg[0] << 24) | ((uint64_t)(uint8_t)cfg[1] << 16) |
+           ((uint64_t)(uint8_t)cfg[2] << 8) | (uint64_t)(uint8_t)cfg[3];
+}
+
+size_t table_bytes(const agis_graph *g, const int32_t cfg[4], bool need_pref, bool need_rowp)
+{
+    (void)cfg;
+    size_t b = sizeof(uint64_t) * (size_t)g->nv;
+    if (need_pref) b += sizeof(uint64_t) * (size_t)g->nv;
+    if (need_rowp) b += sizeof(uint64_t) * (size_t)g->nnz;
+    return b;
+}
+
+void free_table(WeightTable &t)
+{
+    cudaFree(t.q);
+    cudaFree(t.pref);
+    cudaFree(t.rowp);
+    t.q = t.pref = t.rowp = nullptr;
+    t.bytes = 0;
+}
+
+// Builds (or extends) the table of one step configuration.  Caller holds g->mu.
+int build_weight_table(agis_graph *g, const int32_t cfg[4], bool need_pref, bool need_rowp,
+                       WeightTable **out)
+{
+    if (!g->prepped) return AGIS_ERR_STATE;
+    cudaStream_t st = g->ctx->stream;
+    const uint64_t key = cfg_key(cfg);
+    auto it = g->tables.find(key);
+    WeightTable *t;
+    if (it == g->tables.end()) {
+        WeightTable fresh;
+        std::memcpy(fresh.cfg, cfg, sizeof(fresh.cfg));
+        t = &g->tables.emplace(key, fresh).first->second;
+        const int64_t nv = g->nv;
+        AGIS_CUDA_TRY(cudaMalloc(&t->q, sizeof(uint64_t) * (size_t)(nv > 0 ? nv : 1)));
+        t->bytes = sizeof(uint64_t) * (size_t)nv;
+        unsigned long long *d_max = nullptr;
+        AGIS_CUDA_TRY(cudaMallocAsync(&d_max, sizeof(unsigned long long), st));
+        AGIS_CUDA_TRY(cudaMemsetAsync(d_max, 0, sizeof(unsigned long long), st));
+        const int blocks = grid_stride_blocks(g, nv, 256);
+        count_launch();
+        k_weight_max<<<blocks, 256, 0, st>>>(g->off, g->nsum, g->hits, nv, g->c_min, cfg[0], cfg[1],
+                                             cfg[2], cfg[3], d_max);
+        unsigned long long bits = 0;
+        AGIS_CUDA_TRY(cudaMemcpyAsync(&bits, d_max, sizeof(bits), cudaMemcpyDeviceToHost, st));
+        AGIS_CUDA_TRY(cudaStreamSynchronize(st));
+        cudaFreeAsync(d_max, st);
+        double wmax;
+        std::memcpy(&wmax, &bits, sizeof(wmax));
+        // scale so that max weight < 2^K, K = 62 - ceil(log2(nv + 1)): every sum of
+        // quantised weights stays below 2^62
+        int expo = 0;
+        if (wmax > 0.0) std::frexp(wmax, &expo);
+        int lg = 0;
+        while (lg < 63 && (1ull << lg) < (uint64_t)(nv + 1)) ++lg;
+        t->shift = (62 - lg) - expo;
+        count_launch();
+        k_weight_quantise<<<blocks, 256, 0, st>>>(g->off, g->nsum, g->hits, nv, g->c_min, cfg[0],
+                                                  cfg[1], cfg[2], cfg[3], t->shift, t->q);
+        AGIS_CUDA_TRY(cudaGetLastError());
+    } else {
+        t = &it->second;
+    }
+    if (need_pref && !t->pref) {
+        AGIS_CUDA_TRY(cudaMalloc(&t->pref, sizeof(uint64_t) * (size_t)(g->nv > 0 ? g->nv : 1)));
+        t->bytes += sizeof(uint64_t) * (size_t)g->nv;
+        int rc = inclusive_scan(g, t->q, g->nv, t->pref);
+        if (rc != AGIS_OK) return rc;
+        if (g->nv > 0)
+            AGIS_CUDA_TRY(cudaMemcpyAsync(&t->total, t->pref + (g->nv - 1), sizeof(uint64_t),
+                                          cudaMemcpyDeviceToHost, st));
+        AGIS_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    if (need_rowp && !t->rowp) {
+        AGIS_CUDA_TRY(cudaMalloc(&t->rowp, sizeof(uint64_t) * (size_t)(g->nnz > 0 ? g->nnz : 1)));
+        t->bytes += sizeof(uint64_t) * (size_t)g->nnz;
+        const int blocks = grid_stride_blocks(g, g->nv * 32, 256);
+        count_launch();
+        k_row_prefix<<<blocks, 256, 0, st>>>(g->off, g->cols, g->nv, t->q, t->rowp);
+        AGIS_CUDA_TRY(cudaGetLastError());
+    }
+    t->last_use = ++g->use_clock;
+    *out = t;
+    return AGIS_OK;
+}
+
+}  // namespace agis
+
+using namespace agis;
+
+extern "C" int agis_graph_load_csr(agis_ctx *ctx, const void *offsets, int offsets_are_64bit,
+                                   const int32_t *cols, int64_t nv, int64_t nnz, int on_device,
+                                   int validate, agis_graph **out)
+{
+    if (!ctx || !out || !offsets || (nnz > 0 && !cols) || nv < 1 || nnz < 0 || nv > INT32_MAX)
+        return AGIS_ERR_ARG;
+    *out = nullptr;
+    AGIS_CUDA_TRY(cudaSetDevice(ctx->device));
+    cudaStream_t st = ctx->stream;
+    agis_graph *g = new (std::nothrow) agis_graph();
+    if (!g) return AGIS_ERR_NOMEM;
+    g->ctx = ctx;
+    g->nv = nv;
+    g->nnz = nnz;
+    auto fail = [&](int rc) { cudaFree(g->off); cudaFree(g->cols); delete g; return rc; };
+    if (cudaMalloc(&g->off, sizeof(int64_t) * (size_t)(nv + 1)) != cudaSuccess) return fail(AGIS_ERR_NOMEM);
+    if (cudaMalloc(&g->cols, sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1)) != cudaSuccess)
+        return fail(AGIS_ERR_NOMEM);
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (offsets_are_64bit) {
+        if (cudaMemcpyAsync(g->off, offsets, sizeof(int64_t) * (size_t)(nv + 1), kind, st) != cudaSuccess)
+            return fail(AGIS_ERR_CUDA);
+    } else {
+        // widen int32 offsets on the host side of the copy
+        std::vector<int64_t> wide((size_t)nv + 1);
+        std::vector<int32_t> narrow;
+        const int32_t *src = (const int32_t *)offsets;
+        if (on_device) {
+            narrow.resize((size_t)nv + 1);
+            if (cudaMemcpy(narrow.data(), offsets, sizeof(int32_t) * (size_t)(nv + 1),
+                           cudaMemcpyDeviceToHost) != cudaSuccess)
+                return fail(AGIS_ERR_CUDA);
+            src = narrow.data();
+        }
+        for (int64_t i = 0; i <= nv; ++i) wide[(size_t)i] = src[i];
+        if (cudaMemcpyAsync(g->off, wide.data(), sizeof(int64_t) * (size_t)(nv + 1),
+                            cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return fail(AGIS_ERR_CUDA);
+    }
+    if (nnz > 0 && cudaMemcpyAsync(g->cols, cols, sizeof(int32_t) * (size_t)nnz, kind, st) != cudaSuccess)
+        return fail(AGIS_ERR_CUDA);
+    int *d_err = nullptr;
+    if (cudaMalloc(&d_err, sizeof(int)) != cudaSuccess) return fail(AGIS_ERR_NOMEM);
+    cudaMemsetAsync(d_err, 0, sizeof(int), st);
+    const int blocks = grid_stride_blocks(g, nv + 1, 256);
+    count_launch();
+    k_check_offsets<<<blocks, 256, 0, st>>>(g->off, nv, nnz, d_err);
+    int err = 0;
+    cudaMemcpyAsync(&err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) { cudaFree(d_err); return fail(AGIS_ERR_CUDA); }
+    if (err) { cudaFree(d_err); return fail(AGIS_ERR_GRAPH); }
+    if (validate) {
+        count_launch();
+        k_check_rows<<<grid_stride_blocks(g, nv * 32, 256), 256, 0, st>>>(g->off, g->cols, nv, d_err);
+        cudaMemcpyAsync(&err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (cudaStreamSynchronize(st) != cudaSuccess) { cudaFree(d_err); return fail(AGIS_ERR_CUDA); }
+        if (err) { cudaFree(d_err); return fail(AGIS_ERR_GRAPH); }
+    }
+    cudaFree(d_err);
+    {
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) g->rowp_budget = total_b / 4;
+    }
+    // max degree (host side, from the offsets)
+    {
+        std::vector<int64_t> h((size_t)nv + 1);
+        if (cudaMemcpy(h.data(), g->off, sizeof(int64_t) * (size_t)(nv + 1), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return fail(AGIS_ERR_CUDA);
+        int64_t m = 0;
+        for (int64_t v = 0; v < nv; ++v) m = std::max(m, h[(size_t)v + 1] - h[(size_t)v]);
+        g->max_deg = m;
+    }
+    *out = g;
+    return AGIS_OK;
+}
+
+extern "C" int agis_graph_preprocess(agis_graph *g, uint64_t seed, double c_min)
+{
+    if (!g || !(c_min > 0.0) || c_min > 1.0) return AGIS_ERR_ARG;
+    std::lock_guard<std::recursive_mutex> lk(g->mu);
+    AGIS_CUDA_TRY(cudaSetDevice(g->ctx->device));
+    cudaStream_t st = g->ctx->stream;
+    for (auto &kv : g->tables) free_table(kv.second);
+    g->tables.clear();
+    if (!g->nsum) AGIS_CUDA_TRY(cudaMalloc(&g->nsum, sizeof(uint64_t) * (size_t)g->nv));
+    if (!g->hits) AGIS_CUDA_TRY(cudaMalloc(&g->hits, sizeof(uint32_t) * (size_t)g->nv));
+    const int blocks = grid_stride_blocks(g, g->nv * 32, 256);
+    count_launch();
+    k_neighbour_degree_sum<<<blocks, 256, 0, st>>>(g->off, g->cols, g->nv, g->nsum);
+    count_launch();
+    k_cluster_hits<<<blocks, 256, 0, st>>>(g->off, g->cols, g->nv, seed, g->hits);
+    AGIS_CUDA_TRY(cudaGetLastError());
+    AGIS_CUDA_TRY(cudaStreamSynchronize(st));
+    g->prepped = true;
+    g->c_min = c_min;
+    g->prep_seed = seed;
+    return AGIS_OK;
+}
+
+extern "C" int agis_graph_info(const agis_graph *g, int64_t *nv, int64_t *nnz, int64_t *max_degree,
+                               uint64_t *device_bytes)
+{
+    if (!g) return AGIS_ERR_ARG;
+    if (nv) *nv = g->nv;
+    if (nnz) *nnz = g->nnz;
+    if (max_degree) *max_degree = g->max_deg;
+    if (device_bytes) {
+        uint64_t b = 8ull * (uint64_t)(g->nv + 1) + 4ull * (uint64_t)g->nnz;
+        if (g->nsum) b += 12ull * (uint64_t)g->nv;
+        for (const auto &kv : g->tables) b += kv.second.bytes;
+        *device_bytes = b;
+    }
+    return AGIS_OK;
+}
+
+extern "C" int agis_graph_stats_copy(const agis_graph *g, uint64_t *nsum, uint32_t *hits)
+{
+    if (!g) return AGIS_ERR_ARG;
+    if (!g->prepped) return AGIS_ERR_STATE;
+    AGIS_CUDA_TRY(cudaSetDevice(g->ctx->device));
+    AGIS_CUDA_TRY(cudaStreamSynchronize(g->ctx->stream));
+    if (nsum) AGIS_CUDA_TRY(cudaMemcpy(nsum, g->nsum, sizeof(uint64_t) * (size_t)g->nv, cudaMemcpyDeviceToHost));
+    if (hits) AGIS_CUDA_TRY(cudaMemcpy(hits, g->hits, sizeof(uint32_t) * (size_t)g->nv, cudaMemcpyDeviceToHost));
+    return AGIS_OK;
+}
+
+extern "C" int agis_graph_weight_table(agis_graph *g, const int32_t cfg[4], uint64_t *q,
+                                       uint64_t *prefix, int32_t *shift)
+{
+    if (!g || !cfg) return AGIS_ERR_ARG;
+    for (int i = 0; i < 4; ++i) if (cfg[i] < 0 || cfg[i] > 64) return AGIS_ERR_ARG;
+    std::lock_guard<std::recursive_mutex> lk(g->mu);
+    AGIS_CUDA_TRY(cudaSetDevice(g->ctx->device));
+    WeightTable *t = nullptr;
+    int rc = build_weight_table(g, cfg, prefix != nullptr, false, &t);
+    if (rc != AGIS_OK) return rc;
+    AGIS_CUDA_TRY(cudaStreamSynchronize(g->ctx->stream));
+    if (q) AGIS_CUDA_TRY(cudaMemcpy(q, t->q, sizeof(uint64_t) * (size_t)g->nv, cudaMemcpyDeviceToHost));
+    if (prefix) AGIS_CUDA_TRY(cudaMemcpy(prefix, t->pref, sizeof(uint64_t) * (size_t)g->nv, cudaMemcpyDeviceToHost));
+    if (shift) *shift = t->shift;
+    return AGIS_OK;
+}
+
+extern "C" int agis_graph_row_prefix(agis_graph *g, const int32_t cfg[4], uint64_t *row_prefix)
+{
+    if (!g || !cfg || !row_prefix) return AGIS_ERR_ARG;
+    for (int i = 0; i < 4; ++i) if (cfg[i] < 0 || cfg[i] > 64) return AGIS_ERR_ARG;
+    std::lock_guard<std::recursive_mutex> lk(g->mu);
+    AGIS_CUDA_TRY(cudaSetDevice(g->ctx->device));
+    WeightTable *t = nullptr;
+    int rc = build_weight_table(g, cfg, false, true, &t);
+    if (rc != AGIS_OK) return rc;
+    AGIS_CUDA_TRY(cudaStreamSynchronize(g->ctx->stream));
+    AGIS_CUDA_TRY(cudaMemcpy(row_prefix, t->rowp, sizeof(uint64_t) * (size_t)g->nnz, cudaMemcpyDeviceToHost));
+    return AGIS_OK;
+}
+
+extern "C" int agis_graph_drop_tables(agis_graph *g)
+{
+    if (!g) return AGIS_ERR_ARG;
+    std::lock_guard<std::recursive_mutex> lk(g->mu);
+    cudaSetDevice(g->ctx->device);
+    cudaStreamSynchronize(g->ctx->stream);
+    for (auto it = g->tables.begin(); it != g->tables.end();) {
+        if (it->second.pins > 0) { ++it; continue; }
+        free_table(it->second);
+        it = g->tables.erase(it);
+    }
+    return AGIS_OK;
+}
+
+extern "C" int agis_graph_validate(agis_graph *g)
+{
+    if (!g) return AGIS_ERR_ARG;
+    std::lock_guard<std::recursive_mutex> lk(g->mu);
+    AGIS_CUDA_TRY(cudaSetDevice(g->ctx->device));
+    cudaStream_t st = g->ctx->stream;
+    int *d_err = nullptr;
+    AGIS_CUDA_TRY(cudaMalloc(&d_err, sizeof(int)));
+    cudaMemsetAsync(d_err, 0, sizeof(int), st);
+    count_launch();
+    k_check_offsets<<<grid_stride_blocks(g, g->nv + 1, 256), 256, 0, st>>>(g->off, g->nv, g->nnz, d_err);
+    int err = 0;
+    cudaMemcpyAsync(&err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess && !err) {
+        count_launch();
+        k_check_rows<<<grid_stride_blocks(g, g->nv * 32, 256), 256, 0, st>>>(g->off, g->cols, g->nv, d_err);
+        cudaMemcpyAsync(&err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
+        e = cudaStreamSynchronize(st);
+    }
+    cudaFree(d_err);
+    if (e != cudaSuccess) return AGIS_ERR_CUDA;
+    return err ? AGIS_ERR_GRAPH : AGIS_OK;
+}
+
+extern "C" int agis_graph_copy_csr(const agis_graph *g, int64_t *off, int32_t *cols)
+{
+    if (!g) return AGIS_ERR_ARG;
+    AGIS_CUDA_TRY(cudaSetDevice(g->ctx->device));
+    AGIS_CUDA_TRY(cudaStreamSynchronize(g->ctx->stream));
+    if (off) AGIS_CUDA_TRY(cudaMemcpy(off, g->off, sizeof(int64_t) * (size_t)(g->nv + 1), cudaMemcpyDeviceToHost));
+    if (cols && g->nnz > 0)
+        AGIS_CUDA_TRY(cudaMemcpy(cols, g->cols, sizeof(int32_t) * (size_t)g->nnz, cudaMemcpyDeviceToHost));
+    return AGIS_OK;
+}

@@ -1,0 +1,664 @@
+// Host runtime: contexts, query compilation into device descriptors, the adaptive
+// Alg. 1 loop (plain per-query launches), the batched loop that replays one captured
+// CUDA graph per epoch, per-trial dumps, and device-resident fixed-budget sampling.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "agis_internal.h"
+
+namespace agis {
+
+std::atomic<uint64_t> g_launches{0};
+
+double now_s()
+{
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+namespace {
+
+template <typename T>
+int grow_device(T **p, size_t *cap, size_t need, uint64_t *generation)
+{
+    if (need <= *cap) return AGIS_OK;
+    size_t n = std::max<size_t>(need, *cap * 2);
+    n = std::max<size_t>(n, 64);
+    cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    AGIS_CUDA_TRY(cudaMalloc(p, sizeof(T) * n));
+    *cap = n;
+    ++*generation;
+    return AGIS_OK;
+}
+
+template <typename T>
+int grow_pinned(T **p, size_t *cap, size_t need, uint64_t *generation)
+{
+    if (need <= *cap) return AGIS_OK;
+    size_t n = std::max<size_t>(need, *cap * 2);
+    n = std::max<size_t>(n, 64);
+    cudaFreeHost(*p);
+    *p = nullptr;
+    *cap = 0;
+    AGIS_CUDA_TRY(cudaMallocHost(p, sizeof(T) * n));
+    *cap = n;
+    ++*generation;
+    return AGIS_OK;
+}
+
+void free_buffers(LaunchBuffers &lb)
+{
+    if (lb.exec) cudaGraphExecDestroy(lb.exec);
+    if (lb.graph) cudaGraphDestroy(lb.graph);
+    cudaFree(lb.d_queries);
+    cudaFree(lb.d_items);
+    cudaFree(lb.d_out);
+    cudaFree(lb.d_counter);
+    cudaFree(lb.d_scratch);
+    cudaFreeHost(lb.h_queries);
+    cudaFreeHost(lb.h_items);
+    cudaFreeHost(lb.h_out);
+    cudaFreeHost(lb.h_counter);
+    lb = LaunchBuffers();
+}
+
+// Alg. 1: mu, population sigma^2 (clamped at 0) and eps_hat from N trials.
+void alg1(double n, double sx, double sx2, double z, double *mu, double *var, double *eps_hat)
+{
+    const double m = sx / n;
+    double s2 = sx2 / n - m * m;
+    if (s2 < 0.0) s2 = 0.0;
+    *mu = m;
+    *var = s2;
+    *eps_hat = m > 0.0 ? z * std::sqrt(s2) / std::sqrt(n) / m : INFINITY;
+}
+
+}  // namespace
+
+int check_opts(const agis_opts *o)
+{
+    if (!o) return AGIS_ERR_ARG;
+    if (o->mode < 0 || o->mode > 2) return AGIS_ERR_ARG;
+    if (o->chunk_trials == 0 || o->chunk_trials % kTile != 0) return AGIS_ERR_ARG;
+    if (o->max_trials == 0) return AGIS_ERR_ARG;
+    if (o->eps > 0.0 && !(o->delta > 0.0 && o->delta < 1.0)) return AGIS_ERR_ARG;
+    return AGIS_OK;
+}
+
+int ensure_buffers(LaunchBuffers &lb, size_t n_queries, size_t n_items)
+{
+    int rc;
+    if ((rc = grow_device(&lb.d_queries, &lb.cap_queries, n_queries, &lb.generation))) return rc;
+    if ((rc = grow_device(&lb.d_items, &lb.cap_items, n_items, &lb.generation))) return rc;
+    if ((rc = grow_device(&lb.d_out, &lb.cap_out, 4 * n_items, &lb.generation))) return rc;
+    if (!lb.d_counter) {
+        AGIS_CUDA_TRY(cudaMalloc(&lb.d_counter, 2 * sizeof(uint32_t)));
+        AGIS_CUDA_TRY(cudaMallocHost(&lb.h_counter, 2 * sizeof(uint32_t)));
+        ++lb.generation;
+    }
+    if ((rc = grow_pinned(&lb.h_queries, &lb.hcap_queries, n_queries, &lb.generation))) return rc;
+    if ((rc = grow_pinned(&lb.h_items, &lb.hcap_items, n_items, &lb.generation))) return rc;
+    if ((rc = grow_pinned(&lb.h_out, &lb.hcap_out, 4 * n_items, &lb.generation))) return rc;
+    return AGIS_OK;
+}
+
+// Persistent grid: resident CTAs on every SM (the autotuned count if set), never
+// more than there are items.
+int grid_for(agis_graph *g, size_t n_items)
+{
+    agis_ctx *c = g->ctx;
+    int per_sm = c->blocks_per_sm;
+    if (per_sm <= 0) {
+        int occ = 1;
+        sampler_occupancy(&occ);
+        per_sm = std::max(1, occ);
+    }
+    size_t grid = (size_t)c->sm_count * (size_t)per_sm;
+    grid = std::min(grid, std::max<size_t>(n_items, 1));
+    return (int)grid;
+}
+
+// Bytes of one warp's candidate lists: two lists of cap ids and cap running weights.
+size_t scratch_stride(uint32_t cap)
+{
+    const size_t b = (size_t)cap * 2 * (sizeof(int32_t) + sizeof(uint64_t));
+    return (b + 255) / 256 * 256;
+}
+
+// Per-warp candidate-list scratch for a launch of `grid` CTAs: lists as long as
+// the largest row when that fits in an eighth of device memory (longer anchor
+// rows then take the sampler's list-free path).
+int ensure_scratch(agis_graph *g, LaunchBuffers &lb, int grid)
+{
+    if (lb.d_scratch && lb.scratch_grid >= grid) return AGIS_OK;
+    size_t free_b = 0, total_b = 0;
+    AGIS_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+    const size_t warps = (size_t)grid * kWarps;
+    uint64_t cap = (uint64_t)std::max<int64_t>(g->max_deg, 64);
+    cap = (cap + 63) / 64 * 64;
+    const size_t budget = total_b / 8;
+    while (cap > 64 && scratch_stride((uint32_t)cap) * warps > budget) cap = (cap / 2 + 63) / 64 * 64;
+    cudaFree(lb.d_scratch);
+    lb.d_scratch = nullptr;
+    lb.scratch_bytes = 0;
+    AGIS_CUDA_TRY(cudaMalloc(&lb.d_scratch, scratch_stride((uint32_t)cap) * warps));
+    lb.scratch_bytes = scratch_stride((uint32_t)cap) * warps;
+    lb.scratch_cap = (uint32_t)cap;
+    lb.scratch_grid = grid;
+    ++lb.generation;
+    return AGIS_OK;
+}
+
+int make_dev_query(agis_graph *g, const agis_pattern *p, const agis_opts *o, DevQuery *dq,
+                   double *t_prep)
+{
+    if (!g->prepped) return AGIS_ERR_STATE;
+    uint8_t use[kMaxK];
+    int rc = agis_pattern_decide(p, o->mode, o->beta, use);
+    if (rc != AGIS_OK) return rc;
+    std::memset(dq, 0, sizeof(*dq));
+    dq->k = p->k;
+    dq->seed = o->seed;
+    const double t0 = now_s();
+    bool built = false;
+    for (int i = 0; i < p->k; ++i) {
+        DevStep &s = dq->step[i];
+        s.nb = p->nback[i];
+        s.approx = use[i];
+        for (int j = 0; j < p->nback[i] && j < kMaxK; ++j) s.back[j] = (int8_t)p->back[i][j];
+        if (i >= 2) {
+            // back(i) == back(i-1) + {i-1}?
+            unsigned mi = 0, mp = 0;
+            for (int j = 0; j < p->nback[i]; ++j) mi |= 1u << p->back[i][j];
+            for (int j = 0; j < p->nback[i - 1]; ++j) mp |= 1u << p->back[i - 1][j];
+            s.inc = (int16_t)(mi == (mp | (1u << (i - 1))) ? 1 : 0);
+        }
+        if (!use[i]) continue;
+        const size_t before = g->tables.size();
+        WeightTable *t = nullptr;
+        // a row-prefix table (8 B per CSR entry) makes single-backward draws a search;
+        // past the budget the sampler scans the anchor row instead
+        const bool rowp = i > 0 && p->nback[i] == 1 && (size_t)g->nnz * sizeof(uint64_t) <= g->rowp_budget;
+        rc = build_weight_table(g, p->cfg[i], i == 0, rowp, &t);
+        if (rc != AGIS_OK) return rc;
+        built |= g->tables.size() != before;
+        s.q = t->q;
+        if (i == 0) {
+            s.pref = t->pref;
+            dq->W1 = t->total;
+        } else if (p->nback[i] == 1 && rowp) {
+            s.pref = t->rowp;
+        }
+    }
+    if (!use[0]) dq->W1 = (uint64_t)g->nnz;
+    if (built) AGIS_CUDA_TRY(cudaStreamSynchronize(g->ctx->stream));
+    if (t_prep) *t_prep += now_s() - t0;
+    return AGIS_OK;
+}
+
+int init_run(agis_graph *g, const agis_pattern *p, const agis_opts *o, QueryRun &r)
+{
+    int rc = check_opts(o);
+    if (rc != AGIS_OK) return rc;
+    if (!p) return AGIS_ERR_ARG;
+    r.p = p;
+    r.o = *o;
+    r.z = o->eps > 0.0 ? agis_z_of_delta(o->delta) : 0.0;
+    r.max_tiles = (o->max_trials + kTile - 1) / kTile;
+    r.tiles_per_chunk = o->chunk_trials / kTile;
+    return make_dev_query(g, p, o, &r.dq, &r.t_prep);
+}
+
+// Tiles to run next for one query: the first epoch covers min_trials (whole
+// chunks); later ones aim at the trial count Alg. 1's own formula predicts,
+// N ~ (z sigma / (eps mu))^2, between one chunk and four times the work so far.
+uint64_t next_tiles(const QueryRun &r)
+{
+    const uint64_t left = r.max_tiles - r.done_tiles;
+    if (r.o.eps <= 0.0) return left;
+    const uint64_t tpc = r.tiles_per_chunk;
+    uint64_t want;
+    if (r.done_tiles == 0) {
+        const uint64_t min_tiles = (r.o.min_trials + kTile - 1) / kTile;
+        want = std::max<uint64_t>(tpc, (min_tiles + tpc - 1) / tpc * tpc);
+    } else {
+        const double n = (double)r.trials_done;
+        const double mu = r.sx / n;
+        double var = r.sx2 / n - mu * mu;
+        if (var < 0) var = 0;
+        double need = mu > 0 ? (r.z * r.z * var) / (r.o.eps * r.o.eps * mu * mu) : 4.0 * n;
+        need = std::min(need, 4.0 * n + 1.0);
+        const double more = std::max(need - n, (double)r.o.chunk_trials);
+        want = (uint64_t)std::ceil(more / kTile);
+        want = (want + tpc - 1) / tpc * tpc;
+    }
+    return std::min(want, left);
+}
+
+// Folds the tile sums of tiles [done_tiles, done_tiles + n) (in index order) into
+// the run, evaluating Alg. 1 at each chunk checkpoint.  Stops at the first
+// converged checkpoint.
+void absorb(QueryRun &r, const uint64_t *tiles, uint64_t n)
+{
+    for (uint64_t j = 0; j < n && !r.finished; ++j) {
+        const uint64_t *o = tiles + 4 * j;
+        const uint64_t tile_idx = r.done_tiles;
+        const uint64_t first = tile_idx * kTile;
+        const uint64_t cnt = std::min<uint64_t>(kTile, r.o.max_trials > first ? r.o.max_trials - first : 0);
+        double s, s2;
+        std::memcpy(&s, &o[2], 8);
+        std::memcpy(&s2, &o[3], 8);
+        r.hits += o[0];
+        r.sectors += o[1];
+        r.sx += s;
+        r.sx2 += s2;
+        r.trials_done += cnt;
+        r.done_tiles++;
+        const bool at_ck = (r.done_tiles % r.tiles_per_chunk == 0) || r.done_tiles == r.max_tiles;
+        if (!at_ck) continue;
+        r.ck_trials = r.trials_done;
+        r.ck_hits = r.hits;
+        r.ck_sectors = r.sectors;
+        r.ck_sx = r.sx;
+        r.ck_sx2 = r.sx2;
+        if (r.o.eps > 0.0 && r.trials_done >= r.o.min_trials) {
+            double mu, var, eh;
+            alg1((double)r.trials_done, r.sx, r.sx2, r.z, &mu, &var, &eh);
+            if (mu > 0.0 && eh <= r.o.eps) {
+                r.converged = true;
+                r.finished = true;
+            }
+        }
+        if (r.done_tiles == r.max_tiles) r.finished = true;
+    }
+}
+
+void fill_result(const QueryRun &r, agis_result *out)
+{
+    std::memset(out, 0, sizeof(*out));
+    const double n = (double)r.ck_trials;
+    double mu = 0, var = 0, eh = INFINITY;
+    if (r.ck_trials > 0) alg1(n, r.ck_sx, r.ck_sx2, r.z > 0 ? r.z : agis_z_of_delta(r.o.delta > 0 && r.o.delta < 1 ? r.o.delta : 0.05), &mu, &var, &eh);
+    out->estimate = mu;
+    out->subgraphs = r.p && r.p->aut ? mu / (double)r.p->aut : 0.0;
+    out->mean = mu;
+    out->var = var;
+    out->eps_hat = eh;
+    out->sum_x = r.ck_sx;
+    out->sum_x2 = r.ck_sx2;
+    out->trials = r.ck_trials;
+    out->hits = r.ck_hits;
+    out->sectors = r.ck_sectors;
+    out->converged = r.converged ? 1 : 0;
+    out->launches = r.launches;
+    out->t_prep_s = r.t_prep;
+}
+
+// Stages items for the given runs (tile ranges) into lb's pinned buffers.
+size_t stage_items(LaunchBuffers &lb, std::vector<QueryRun *> &runs, const std::vector<uint64_t> &ntiles)
+{
+    size_t k = 0;
+    for (size_t q = 0; q < runs.size(); ++q) {
+        const QueryRun &r = *runs[q];
+        lb.h_queries[q] = r.dq;
+        for (uint64_t j = 0; j < ntiles[q]; ++j) {
+            const uint64_t tile = r.done_tiles + j;
+            const uint64_t first = tile * kTile;
+            WorkItem &w = lb.h_items[k];
+            w.query = (uint32_t)q;
+            w.count = (uint32_t)std::min<uint64_t>(kTile, r.o.max_trials - first);
+            w.first = first;
+            w.slot = k;
+            ++k;
+        }
+    }
+    return k;
+}
+
+// One epoch by plain stream launches.
+int run_epoch_direct(agis_graph *g, std::vector<QueryRun *> &runs, const std::vector<uint64_t> &ntiles,
+                     size_t total)
+{
+    LaunchBuffers &lb = g->lb;
+    cudaStream_t st = g->ctx->stream;
+    int rc = ensure_buffers(lb, runs.size(), total);
+    if (rc != AGIS_OK) return rc;
+    const size_t n = stage_items(lb, runs, ntiles);
+    lb.h_counter[0] = 0;
+    lb.h_counter[1] = (uint32_t)n;
+    AGIS_CUDA_TRY(cudaMemcpyAsync(lb.d_queries, lb.h_queries, sizeof(DevQuery) * runs.size(), cudaMemcpyHostToDevice, st));
+    AGIS_CUDA_TRY(cudaMemcpyAsync(lb.d_items, lb.h_items, sizeof(WorkItem) * n, cudaMemcpyHostToDevice, st));
+    AGIS_CUDA_TRY(cudaMemcpyAsync(lb.d_counter, lb.h_counter, 2 * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
+    const int grid = grid_for(g, n);
+    if ((rc = ensure_scratch(g, lb, grid)) != AGIS_OK) return rc;
+    rc = launch_sampler(g, lb, grid, nullptr, st, 0, 0, nullptr);
+    if (rc != AGIS_OK) return rc;
+    AGIS_CUDA_TRY(cudaMemcpyAsync(lb.h_out, lb.d_out, sizeof(uint64_t) * 4 * n, cudaMemcpyDeviceToHost, st));
+    AGIS_CUDA_TRY(cudaStreamSynchronize(st));
+    return AGIS_OK;
+}
+
+// The batched epoch as a CUDA graph: H2D of queries, items and counters, the
+// persistent sampler, D2H of the tile sums.  Built once per buffer generation and
+// grid; sizes are patched per epoch.
+int run_epoch_graph(agis_graph *g, std::vector<QueryRun *> &runs, const std::vector<uint64_t> &ntiles,
+                    size_t total)
+{
+    LaunchBuffers &lb = g->lb;
+    cudaStream_t st = g->ctx->stream;
+    int rc = ensure_buffers(lb, runs.size(), total);
+    if (rc != AGIS_OK) return rc;
+    const size_t n = stage_items(lb, runs, ntiles);
+    lb.h_counter[0] = 0;
+    lb.h_counter[1] = (uint32_t)n;
+    const int grid = grid_for(g, (size_t)g->ctx->sm_count * 64);
+    if ((rc = ensure_scratch(g, lb, grid)) != AGIS_OK) return rc;
+    if (!lb.exec || lb.graph_generation != lb.generation || lb.graph_grid != grid) {
+        if (lb.exec) cudaGraphExecDestroy(lb.exec);
+        if (lb.graph) cudaGraphDestroy(lb.graph);
+        lb.exec = nullptr;
+        lb.graph = nullptr;
+        AGIS_CUDA_TRY(cudaGraphCreate(&lb.graph, 0));
+        AGIS_CUDA_TRY(cudaGraphAddMemcpyNode1D(&lb.n_h2d_q, lb.graph, nullptr, 0, lb.d_queries, lb.h_queries,
+                                               sizeof(DevQuery), cudaMemcpyHostToDevice));
+        AGIS_CUDA_TRY(cudaGraphAddMemcpyNode1D(&lb.n_h2d_i, lb.graph, &lb.n_h2d_q, 1, lb.d_items, lb.h_items,
+                                               sizeof(WorkItem), cudaMemcpyHostToDevice));
+        AGIS_CUDA_TRY(cudaGraphAddMemcpyNode1D(&lb.n_h2d_c, lb.graph, &lb.n_h2d_i, 1, lb.d_counter, lb.h_counter,
+                                               2 * sizeof(uint32_t), cudaMemcpyHostToDevice));
+        rc = add_sampler_node(g, lb, grid, lb.graph, &lb.n_h2d_c, 1, &lb.n_kernel);
+        if (rc != AGIS_OK) return rc;
+        AGIS_CUDA_TRY(cudaGraphAddMemcpyNode1D(&lb.n_d2h, lb.graph, &lb.n_kernel, 1, lb.h_out, lb.d_out,
+                                               4 * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+        AGIS_CUDA_TRY(cudaGraphInstantiate(&lb.exec, lb.graph, 0));
+        lb.graph_generation = lb.generation;
+        lb.graph_grid = grid;
+    }
+    AGIS_CUDA_TRY(cudaGraphExecMemcpyNodeSetParams1D(lb.exec, lb.n_h2d_q, lb.d_queries, lb.h_queries,
+                                                     sizeof(DevQuery) * runs.size(), cudaMemcpyHostToDevice));
+    AGIS_CUDA_TRY(cudaGraphExecMemcpyNodeSetParams1D(lb.exec, lb.n_h2d_i, lb.d_items, lb.h_items,
+                                                     sizeof(WorkItem) * std::max<size_t>(n, 1), cudaMemcpyHostToDevice));
+    AGIS_CUDA_TRY(cudaGraphExecMemcpyNodeSetParams1D(lb.exec, lb.n_d2h, lb.h_out, lb.d_out,
+                                                     sizeof(uint64_t) * 4 * std::max<size_t>(n, 1), cudaMemcpyDeviceToHost));
+    count_launch();
+    AGIS_CUDA_TRY(cudaGraphLaunch(lb.exec, st));
+    AGIS_CUDA_TRY(cudaStreamSynchronize(st));
+    return AGIS_OK;
+}
+
+// Drives a set of queries to completion; each epoch is one launch over the next
+// tiles of every unfinished query.  `use_graph` selects the captured-graph epoch.
+int drive(agis_graph *g, std::vector<QueryRun *> &runs, bool use_graph, size_t max_items_per_epoch)
+{
+    const double t0 = now_s();
+    for (;;) {
+        std::vector<QueryRun *> active;
+        std::vector<uint64_t> ntiles;
+        size_t total = 0;
+        for (QueryRun *r : runs) {
+            if (r->finished) continue;
+            uint64_t n = next_tiles(*r);
+            if (n == 0) { r->finished = true; continue; }
+            active.push_back(r);
+            ntiles.push_back(n);
+            total += n;
+        }
+        if (active.empty()) break;
+        if (max_items_per_epoch && total > max_items_per_epoch) {
+            // shrink proportionally, keeping whole chunks and at least one chunk each
+            const double f = (double)max_items_per_epoch / (double)total;
+            total = 0;
+            for (size_t q = 0; q < active.size(); ++q) {
+                const uint64_t tpc = active[q]->tiles_per_chunk;
+                uint64_t n = (uint64_t)((double)ntiles[q] * f) / tpc * tpc;
+                n = std::max<uint64_t>(n, std::min<uint64_t>(tpc, ntiles[q]));
+                ntiles[q] = n;
+                total += n;
+            }
+        }
+        int rc = use_graph ? run_epoch_graph(g, active, ntiles, total) : run_epoch_direct(g, active, ntiles, total);
+        if (rc != AGIS_OK) return rc;
+        size_t k = 0;
+        for (size_t q = 0; q < active.size(); ++q) {
+            active[q]->launches++;
+            absorb(*active[q], g->lb.h_out + 4 * k, ntiles[q]);
+            k += ntiles[q];
+        }
+    }
+    const double dt = now_s() - t0;
+    (void)dt;
+    return AGIS_OK;
+}
+
+}  // namespace agis
+
+using namespace agis;
+
+extern "C" const char *agis_status_str(int s)
+{
+    switch (s) {
+    case AGIS_OK: return "ok";
+    case AGIS_ERR_ARG: return "invalid argument";
+    case AGIS_ERR_NOMEM: return "out of memory";
+    case AGIS_ERR_CUDA: return "CUDA error";
+    case AGIS_ERR_GRAPH: return "invalid graph";
+    case AGIS_ERR_PATTERN: return "invalid pattern";
+    case AGIS_ERR_TIMEOUT: return "timeout";
+    case AGIS_ERR_BUSY: return "busy";
+    case AGIS_ERR_STATE: return "invalid state";
+    default: return "unknown status";
+    }
+}
+
+extern "C" void agis_default_opts(agis_opts *o)
+{
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->eps = 0.1;
+    o->delta = 0.01;
+    o->beta = 0.8;
+    o->mode = AGIS_MODE_AUTO;
+    o->seed = 1;
+    o->min_trials = 65536;
+    o->max_trials = 1ull << 32;
+    o->chunk_trials = 65536;
+}
+
+// Phi^{-1}(1 - delta/2): bisection on the upper tail 0.5 erfc(z / sqrt 2) = delta / 2.
+extern "C" double agis_z_of_delta(double delta)
+{
+    if (!(delta > 0.0 && delta < 1.0)) return NAN;
+    double lo = 0.0, hi = 64.0;
+    for (int it = 0; it < 256 && hi - lo > 0.0; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (mid == lo || mid == hi) break;
+        const double tail = 0.5 * std::erfc(mid / std::sqrt(2.0));
+        if (tail > 0.5 * delta) lo = mid; else hi = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+extern "C" int agis_create(int device, void *cuda_stream, agis_ctx **out)
+{
+    if (!out) return AGIS_ERR_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return AGIS_ERR_CUDA;
+    if (device < 0 || device >= ndev) return AGIS_ERR_ARG;
+    AGIS_CUDA_TRY(cudaSetDevice(device));
+    agis_ctx *c = new (std::nothrow) agis_ctx();
+    if (!c) return AGIS_ERR_NOMEM;
+    c->device = device;
+    if (cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+        delete c;
+        return AGIS_ERR_CUDA;
+    }
+    if (cuda_stream) {
+        c->stream = (cudaStream_t)cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete c;
+            return AGIS_ERR_CUDA;
+        }
+        c->own_stream = true;
+    }
+    *out = c;
+    return AGIS_OK;
+}
+
+extern "C" int agis_destroy(agis_ctx *c)
+{
+    if (!c) return AGIS_ERR_ARG;
+    cudaSetDevice(c->device);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return AGIS_OK;
+}
+
+extern "C" int agis_graph_free(agis_graph *g)
+{
+    if (!g) return AGIS_ERR_ARG;
+    {
+        std::lock_guard<std::recursive_mutex> lk(g->mu);
+        cudaSetDevice(g->ctx->device);
+        cudaStreamSynchronize(g->ctx->stream);
+        for (auto &kv : g->tables) free_table(kv.second);
+        g->tables.clear();
+        free_buffers(g->lb);
+        cudaFree(g->off);
+        cudaFree(g->cols);
+        cudaFree(g->nsum);
+        cudaFree(g->hits);
+    }
+    delete g;
+    return AGIS_OK;
+}
+
+extern "C" int agis_estimate(agis_graph *g, const agis_pattern *p, const agis_opts *opts, agis_result *out)
+{
+    if (!g || !p || !opts || !out) return AGIS_ERR_ARG;
+    std::lock_guard<std::recursive_mutex> lk(g->mu);
+    AGIS_CUDA_TRY(cudaSetDevice(g->ctx->device));
+    QueryRun r;
+    int rc = init_run(g, p, opts, r);
+    if (rc != AGIS_OK) return rc;
+    const double t0 = now_s();
+    std::vector<QueryRun *> runs{&r};
+    rc = drive(g, runs, false, 0);
+    if (rc != AGIS_OK) return rc;
+    fill_result(r, out);
+    out->t_sample_s = now_s() - t0;
+    return AGIS_OK;
+}
+
+extern "C" int agis_estimate_batch(agis_graph *g, int n, const agis_pattern *const *patterns,
+                                   const agis_opts *opts, agis_result *out)
+{
+    if (!g || n < 0 || (n > 0 && (!patterns || !opts || !out))) return AGIS_ERR_ARG;
+    if (n == 0) return AGIS_OK;
+    std::lock_guard<std::recursive_mutex> lk(g->mu);
+    AGIS_CUDA_TRY(cudaSetDevice(g->ctx->device));
+    std::vector<QueryRun> rs((size_t)n);
+    for (int i = 0; i < n; ++i) {
+        int rc = init_run(g, patterns[i], &opts[i], rs[(size_t)i]);
+        if (rc != AGIS_OK) return rc;
+    }
+    const double t0 = now_s();
+    std::vector<QueryRun *> runs;
+    for (auto &r : rs) runs.push_back(&r);
+    int rc = drive(g, runs, true, 0);
+    if (rc != AGIS_OK) return rc;
+    const double dt = now_s() - t0;
+    for (int i = 0; i < n; ++i) {
+        fill_result(rs[(size_t)i], &out[i]);
+        out[i].t_sample_s = dt;
+    }
+    return AGIS_OK;
+}
+
+extern "C" int agis_dump_trials(agis_graph *g, const agis_pattern *p, const agis_opts *opts, uint64_t first,
+                                uint64_t count, int32_t *emb, uint8_t *hit, double *x, uint64_t *sectors)
+{
+    if (!g || !p || !opts) return AGIS_ERR_ARG;
+    if (count == 0) return AGIS_OK;
+    std::lock_guard<std::recursive_mutex> lk(g->mu);
+    AGIS_CUDA_TRY(cudaSetDevice(g->ctx->device));
+    cudaStream_t st = g->ctx->stream;
+    DevQuery dq;
+    int rc = make_dev_query(g, p, opts, &dq, nullptr);
+    if (rc != AGIS_OK) return rc;
+    const uint64_t ntiles = (count + kTile - 1) / kTile;
+    LaunchBuffers &lb = g->lb;
+    rc = ensure_buffers(lb, 1, ntiles);
+    if (rc != AGIS_OK) return rc;
+    DumpView dv{nullptr, nullptr, nullptr, nullptr, first};
+    const size_t c = (size_t)count;
+    auto cleanup = [&]() { cudaFree(dv.emb); cudaFree(dv.hit); cudaFree(dv.x); cudaFree(dv.sectors); };
+    if ((emb && cudaMalloc(&dv.emb, sizeof(int32_t) * kMaxK * c) != cudaSuccess) ||
+        (hit && cudaMalloc(&dv.hit, c) != cudaSuccess) ||
+        (x && cudaMalloc(&dv.x, sizeof(double) * c) != cudaSuccess) ||
+        (sectors && cudaMalloc(&dv.sectors, sizeof(uint64_t) * c) != cudaSuccess)) {
+        cleanup();
+        return AGIS_ERR_NOMEM;
+    }
+    lb.h_queries[0] = dq;
+    lb.h_counter[0] = 0;
+    lb.h_counter[1] = (uint32_t)ntiles;
+    cudaMemcpyAsync(lb.d_queries, lb.h_queries, sizeof(DevQuery), cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(lb.d_counter, lb.h_counter, 2 * sizeof(uint32_t), cudaMemcpyHostToDevice, st);
+    const int grid = grid_for(g, ntiles);
+    if (rc == AGIS_OK) rc = ensure_scratch(g, lb, grid);
+    if (rc == AGIS_OK) rc = launch_sampler(g, lb, grid, &dv, st, first, count, nullptr);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (rc == AGIS_OK && e != cudaSuccess) rc = AGIS_ERR_CUDA;
+    if (rc == AGIS_OK && emb && cudaMemcpy(emb, dv.emb, sizeof(int32_t) * kMaxK * c, cudaMemcpyDeviceToHost) != cudaSuccess) rc = AGIS_ERR_CUDA;
+    if (rc == AGIS_OK && hit && cudaMemcpy(hit, dv.hit, c, cudaMemcpyDeviceToHost) != cudaSuccess) rc = AGIS_ERR_CUDA;
+    if (rc == AGIS_OK && x && cudaMemcpy(x, dv.x, sizeof(double) * c, cudaMemcpyDeviceToHost) != cudaSuccess) rc = AGIS_ERR_CUDA;
+    if (rc == AGIS_OK && sectors && cudaMemcpy(sectors, dv.sectors, sizeof(uint64_t) * c, cudaMemcpyDeviceToHost) != cudaSuccess) rc = AGIS_ERR_CUDA;
+    cleanup();
+    return rc;
+}
+
+extern "C" int agis_sample_device(agis_graph *g, const agis_pattern *p, const agis_opts *opts, uint64_t first,
+                                  uint64_t ntiles, uint64_t *tile_out)
+{
+    if (!g || !p || !opts || !tile_out || ntiles == 0 || ntiles > 0xffffffffull) return AGIS_ERR_ARG;
+    std::lock_guard<std::recursive_mutex> lk(g->mu);
+    AGIS_CUDA_TRY(cudaSetDevice(g->ctx->device));
+    cudaStream_t st = g->ctx->stream;
+    int rc = check_opts(opts);
+    if (rc != AGIS_OK) return rc;
+    LaunchBuffers &lb = g->lb;
+    rc = ensure_buffers(lb, 1, 1);
+    if (rc != AGIS_OK) return rc;
+    DevQuery dq;
+    rc = make_dev_query(g, p, opts, &dq, nullptr);
+    if (rc != AGIS_OK) return rc;
+    // pageable sources: the runtime stages them before the call returns, so back to
+    // back calls never wait for the device (the copies are stream-ordered after the
+    // previous launch, which is what keeps the shared device slots safe)
+    const uint32_t counter[2] = {0u, (uint32_t)ntiles};
+    AGIS_CUDA_TRY(cudaMemcpyAsync(lb.d_queries, &dq, sizeof(DevQuery), cudaMemcpyHostToDevice, st));
+    AGIS_CUDA_TRY(cudaMemcpyAsync(lb.d_counter, counter, sizeof(counter), cudaMemcpyHostToDevice, st));
+    const int grid = grid_for(g, ntiles);
+    if ((rc = ensure_scratch(g, lb, grid)) != AGIS_OK) return rc;
+    return launch_sampler(g, lb, grid, nullptr, st, first, ntiles * kTile, tile_out);
+}
+
+extern "C" int agis_prepare(agis_graph *g, const agis_pattern *p, const agis_opts *opts)
+{
+    if (!g || !p || !opts) return AGIS_ERR_ARG;
+    int rc = check_opts(opts);
+    if (rc != AGIS_OK) return rc;
+    std::lock_guard<std::recursive_mutex> lk(g->mu);
+    AGIS_CUDA_TRY(cudaSetDevice(g->ctx->device));
+    DevQuery dq;
+    rc = make_dev_query(g, p, opts, &dq, nullptr);
+    if (rc != AGIS_OK) return rc;
+    return cuda_status(cudaStreamSynchronize(g->ctx->stream));
+}
+
+extern "C" uint64_t agis_kernel_launches(void) { return g_launches.load(); }

@@ -1,0 +1,622 @@
+// The sampler: Alg. 3 (structure-informed neighbour sampling) with one warp per
+// trial, persistent CTAs pulling work items (1024-trial tiles of any query) from a
+// device counter, and a fixed-order FP64 reduction of each tile.
+//
+// Per step i of a trial (tau = v_1..v_{i-1} so far):
+//   step 1        draw over all vertices: f_approx by the inclusive prefix of the
+//                 quantised weights, f_uniform by the CSR offsets (edge-uniform);
+//   |B[i]| = 1    S = N(a) \ tau for the backward neighbour a: the trajectory
+//                 members found in a's row are excluded and the draw is a k-ary
+//                 warp search over a's row prefix (f_approx) or over positions;
+//   |B[i]| >= 2   S = intersection of the backward rows minus tau: the warp scans
+//                 the shortest backward row 32 entries at a time and checks every
+//                 entry in the other rows by binary search (closing-edge checks),
+//                 then draws from the survivors' weights.
+// A draw is r = floor(U * W / 2^128) with U from Philox4x64-10 at counter
+// (trial, i, 1, 0), key (seed, 0); the chosen vertex is the first candidate in
+// ascending id order whose inclusive running weight exceeds r; X is multiplied by
+// W / q(v).  Every integer step is exact, so the device reproduces the CPU
+// restatement trial for trial.
+#include <cstdio>
+
+#include "agis_internal.h"
+#include "philox.cuh"
+
+namespace agis {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// ---------------------------------------------------------------- cost model
+// Sectors of a search over L entries of w bytes: ceil(log2(ceil(L*w/32))) + 1.
+__device__ __forceinline__ uint64_t sec_search(int64_t L, int w)
+{
+    const uint64_t bytes = (uint64_t)(L > 0 ? L : 1) * (uint64_t)w;
+    if (bytes <= 32) return 1;
+    const uint64_t n = (bytes + 31) / 32;
+    return (uint64_t)(64 - __clzll((long long)(n - 1))) + 1;
+}
+
+// Sectors to test d_a entries for membership in a row of m entries: the cheaper of
+// reading the row once (a merge) and one search per entry.
+__device__ __forceinline__ uint64_t row_check_sectors(int64_t da, int64_t m)
+{
+    const uint64_t merge = (uint64_t)((4 * (m > 0 ? m : 1) + 31) / 32);
+    const uint64_t search = (uint64_t)da * sec_search(m, 4);
+    return merge < search ? merge : search;
+}
+
+// ---------------------------------------------------------------- searches
+
+// Last position with row[pos] <= x, or -1 if x is absent; the probe count depends
+// only on d, so lanes searching the same row stay converged.
+__device__ __forceinline__ int64_t row_find(const int32_t *row, int64_t d, int32_t x)
+{
+    if (d <= 0) return -1;
+    int64_t lo = 0, len = d;
+    while (len > 1) {
+        const int64_t half = len >> 1;
+        if (__ldg(row + lo + half) <= x) lo += half;
+        len -= half;
+    }
+    return __ldg(row + lo) == x ? lo : -1;
+}
+
+// Sum of the excluded weights at positions <= pos.  The excluded positions and
+// weights live one per lane (bits of xmask); all lanes must call this together.
+__device__ __forceinline__ uint64_t excluded_upto(int64_t pos, uint32_t xmask, int64_t xp, uint64_t xq)
+{
+    uint64_t s = 0;
+    while (xmask) {
+        const int src = __ffs(xmask) - 1;
+        xmask &= xmask - 1;
+        const int64_t p = __shfl_sync(kFull, xp, src);
+        const uint64_t q = __shfl_sync(kFull, xq, src);
+        if (p <= pos) s += q;
+    }
+    return s;
+}
+
+// First index j in [0, n) with F(j) > r, where F(j) = P[j] - (excluded weight at
+// positions <= j), or F(j) = j + 1 - (excluded count ...) when P is null.  F is
+// non-decreasing and F(n-1) > r.  Each round splits the range into 32 parts and
+// one ballot picks the part, so a row of d entries takes ceil(log32 d) rounds.
+__device__ int64_t warp_find(const uint64_t *P, int64_t n, uint64_t r, uint32_t xmask, int64_t xp,
+                             uint64_t xq, int lane)
+{
+    int64_t lo = 0, hi = n;
+    while (hi - lo > 32) {
+        const int64_t step = (hi - lo + 31) >> 5;
+        const int64_t pos = lo + (int64_t)(lane + 1) * step - 1;
+        const int64_t cpos = pos < hi - 1 ? pos : hi - 1;
+        const uint64_t ex = excluded_upto(cpos, xmask, xp, xq);
+        bool gt = true;
+        if (pos < hi - 1) {
+            const uint64_t f = (P ? __ldg(P + pos) : (uint64_t)(pos + 1)) - ex;
+            gt = f > r;
+        }
+        const int f = __ffs(__ballot_sync(kFull, gt)) - 1;
+        const int64_t nlo = lo + (int64_t)f * step;
+        const int64_t nhi = lo + (int64_t)(f + 1) * step;
+        lo = nlo;
+        hi = nhi < hi ? nhi : hi;
+    }
+    const int64_t pos = lo + lane;
+    const int64_t cpos = pos < hi ? pos : hi - 1;
+    const uint64_t ex = excluded_upto(cpos, xmask, xp, xq);
+    bool gt = true;
+    if (pos < hi) gt = ((P ? __ldg(P + pos) : (uint64_t)(pos + 1)) - ex) > r;
+    return lo + (__ffs(__ballot_sync(kFull, gt)) - 1);
+}
+
+__device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+__device__ __forceinline__ uint64_t warp_incl_scan(uint64_t v, int lane)
+{
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t n = __shfl_up_sync(kFull, v, o);
+        if (lane >= o) v += n;
+    }
+    return v;
+}
+
+struct TrialOut {
+    double x;
+    uint64_t sectors;
+    int hit;
+};
+
+// One window of the intersection scan: entry `idx` of the anchor row for this
+// lane; returns the lane's candidate weight (0 if not in S) and sets ok / x.
+__device__ __forceinline__ uint64_t window_weight(const GraphView &g, const DevStep &S,
+                                                  const int32_t *tau_s, int i, int64_t a_start,
+                                                  int64_t da, int64_t idx, const int64_t *o_start,
+                                                  const int64_t *o_len, int n_other, bool &ok,
+                                                  int32_t &x)
+{
+    ok = idx < da;
+    x = ok ? __ldg(g.cols + a_start + idx) : -1;
+    if (ok) {
+        for (int j = 0; j < i; ++j) ok &= (x != tau_s[j]);
+    }
+    for (int o = 0; o < n_other; ++o) {
+        if (ok) ok = row_find(g.cols + o_start[o], o_len[o], x) >= 0;
+    }
+    if (!ok) return 0;
+    return S.approx ? __ldg(S.q + x) : 1u;
+}
+
+// Scratch of one warp: two candidate lists (ping-pong), each `cap` vertex ids and
+// the inclusive running weights of the ids kept so far.
+struct WarpSets {
+    int32_t *xs[2];
+    uint64_t *pw[2];
+    uint32_t cap;
+};
+
+// Keeps the entries of the ascending list L[0, n) that are not trajectory members
+// (tau_s[0, tau_n)) and that occur in the ascending row R[0, m) (all of them when R
+// is null); survivors are appended, in order, to out.  With kWeigh the survivors'
+// weights (q[x] under f_approx, 1 under f_uniform) are accumulated into out_pw as
+// inclusive running sums and *W receives the total.
+//
+// Membership in R is found either by a warp merge (R read once, 32 entries per
+// coalesced load, each loaded entry located among the 32 list entries of the window
+// by a shuffle search) or by one binary search per list entry, whichever the sizes
+// make cheaper.
+template <bool kWeigh>
+__device__ uint32_t filter_list(const int32_t *L, uint32_t n, const int32_t *R, int64_t m,
+                                const int32_t *tau_s, int tau_n, int32_t *out, uint64_t *out_pw,
+                                const uint64_t *q, bool approx, uint64_t *W, int lane)
+{
+    bool merge = false;
+    if (R) {
+        int lg = 1;
+        while ((1ll << lg) < m + 1) ++lg;
+        const int64_t merge_loads = ((int64_t)n + m + 31) / 32;
+        const int64_t search_loads = (((int64_t)n + 31) / 32) * lg;
+        merge = merge_loads <= search_loads;
+    }
+    uint32_t cnt = 0;
+    uint64_t carry = 0;
+    int64_t rpos = 0;
+    for (uint32_t base = 0; base < n; base += 32) {
+        const uint32_t idx = base + lane;
+        const bool valid = idx < n;
+        const int32_t x = valid ? L[idx] : 0x7fffffff;
+        bool ok = valid;
+        for (int j = 0; j < tau_n; ++j) ok &= (x != tau_s[j]);
+        if (R) {
+            if (merge) {
+                const int last = (n - base) >= 32 ? 31 : (int)(n - base - 1);
+                const int32_t x_last = __shfl_sync(kFull, x, last);
+                uint32_t found = 0;
+                for (;;) {
+                    const bool rvalid = rpos + lane < m;
+                    const int32_t rv = rvalid ? __ldg(R + rpos + lane) : 0x7fffffff;
+                    // position of rv among the window's entries (lanes 0..last, ascending)
+                    int lo = 0, len = last + 1;
+                    while (len > 1) {
+                        const int half = len >> 1;
+                        const int32_t xv = __shfl_sync(kFull, x, lo + half);
+                        if (xv <= rv) lo += half;
+                        len -= half;
+                    }
+                    const int32_t xlo = __shfl_sync(kFull, x, lo);
+                    uint32_t bit = (rvalid && xlo == rv) ? (1u << lo) : 0u;
+                    for (int o = 16; o > 0; o >>= 1) bit |= __shfl_xor_sync(kFull, bit, o);
+                    found |= bit;
+                    const int c = __popc(__ballot_sync(kFull, rvalid && rv <= x_last));
+                    rpos += c;
+                    if (c < 32) break;
+                }
+                ok = ok && ((found >> lane) & 1u);
+            } else if (ok) {
+                ok = row_find(R, m, x) >= 0;
+            }
+        }
+        const uint32_t bal = __ballot_sync(kFull, ok);
+        const uint32_t pos = cnt + __popc(bal & ((1u << lane) - 1u));
+        if (ok) out[pos] = x;
+        if (kWeigh) {
+            const uint64_t w = ok ? (approx ? __ldg(q + x) : 1u) : 0u;
+            const uint64_t incl = warp_incl_scan(w, lane);
+            if (ok) out_pw[pos] = carry + incl;
+            carry += __shfl_sync(kFull, incl, 31);
+        }
+        cnt += __popc(bal);
+    }
+    if (kWeigh) *W = carry;
+    return cnt;
+}
+
+// Alg. 3 for trial t of query Q; all 32 lanes call it together.  tau_s is the
+// warp's shared-memory copy of the trajectory.
+__device__ TrialOut run_trial(const GraphView &g, const DevQuery &Q, uint64_t t, int32_t *tau_s,
+                              const WarpSets &ws, int lane)
+{
+    TrialOut out{0.0, 0, 0};
+    double X = 1.0;
+    uint64_t sec = 0;
+    int cur = -1;          // scratch list holding S of the previous step (-1: none)
+    uint32_t n_cur = 0;
+    if (lane < kMaxK) tau_s[lane] = -1;
+    __syncwarp();
+    for (int i = 0; i < Q.k; ++i) {
+        const DevStep &S = Q.step[i];
+        uint64_t W = 0, qv = 0;
+        int32_t v = -1;
+        if (i == 0) {
+            // ---- step 1: the whole vertex set
+            W = Q.W1;
+            sec += sec_search(g.nv + 1, 8) + (S.approx ? 1 : 0);
+            if (W == 0) { out.sectors = sec; return out; }
+            const uint64_t r = draw_below(W, t, 1, kStreamTrial, Q.seed);
+            const uint64_t *P = S.approx ? S.pref : (const uint64_t *)(g.off + 1);
+            v = (int32_t)warp_find(P, g.nv, r, 0u, 0, 0, lane);
+            qv = S.approx ? __ldg(S.q + v) : (uint64_t)(__ldg(g.off + v + 1) - __ldg(g.off + v));
+            cur = -1;
+        } else if (S.nb == 1 && (S.pref != nullptr || !S.approx)) {
+            // ---- one backward neighbour: S = N(a) \ tau
+            const int jb = S.back[0];
+            const int32_t a = tau_s[jb];
+            const int64_t a_start = __ldg(g.off + a);
+            const int64_t d = __ldg(g.off + a + 1) - a_start;
+            sec += 1 + (uint64_t)(i - 1) * sec_search(d, 4) + (S.approx ? sec_search(d, 8) + 1 : 0) + 1;
+            // trajectory members inside a's row (lane j checks tau_j)
+            int64_t xp = -1;
+            uint64_t xq = 0;
+            if (lane < i && lane != jb) {
+                const int32_t m = tau_s[lane];
+                xp = row_find(g.cols + a_start, d, m);
+                if (xp >= 0) xq = S.approx ? __ldg(S.q + m) : 1u;
+            }
+            const uint32_t xmask = __ballot_sync(kFull, xp >= 0);
+            const uint64_t excl = warp_sum_u64(xq);
+            const uint64_t *P = S.approx ? S.pref + a_start : nullptr;
+            const uint64_t total = d <= 0 ? 0 : (S.approx ? __ldg(P + d - 1) : (uint64_t)d);
+            W = total - excl;
+            if (W == 0) { out.sectors = sec; return out; }
+            const uint64_t r = draw_below(W, t, (uint64_t)(i + 1), kStreamTrial, Q.seed);
+            const int64_t pos = warp_find(P, d, r, xmask, xp, xq, lane);
+            v = __ldg(g.cols + a_start + pos);
+            qv = S.approx ? __ldg(S.q + v) : 1u;
+            cur = -1;
+        } else {
+            // ---- several backward neighbours (or one, with no row-prefix table):
+            //      intersect, anchored at the shortest row
+            int64_t o_start[kMaxK - 1], o_len[kMaxK - 1];
+            int ai = 0;
+            int64_t a_start = 0, da = -1;
+            for (int b = 0; b < S.nb; ++b) {
+                const int32_t u = tau_s[S.back[b]];
+                const int64_t s0 = __ldg(g.off + u), len = __ldg(g.off + u + 1) - s0;
+                if (da < 0 || len < da) { da = len; ai = b; a_start = s0; }
+            }
+            int n_other = 0;
+            uint64_t search_sec = 0;
+            for (int b = 0; b < S.nb; ++b) {
+                if (b == ai) continue;
+                const int32_t u = tau_s[S.back[b]];
+                o_start[n_other] = __ldg(g.off + u);
+                o_len[n_other] = __ldg(g.off + u + 1) - o_start[n_other];
+                search_sec += row_check_sectors(da, o_len[n_other]);
+                ++n_other;
+            }
+            if (S.nb == 1) {
+                // the cost model counts the method's single-backward draw, whichever way it runs
+                sec += 1 + (uint64_t)(i - 1) * sec_search(da, 4) + (S.approx ? sec_search(da, 8) + 1 : 0) + 1;
+            } else {
+                sec += (uint64_t)S.nb + (uint64_t)((4 * da + 31) / 32) + search_sec;
+            }
+            // S of the previous step is reusable when this step's backward set is the
+            // previous one plus the previous vertex: S_i = S_{i-1} & N(v_{i-1})
+            const bool reuse = S.inc && cur >= 0;
+            const uint32_t n_src = reuse ? n_cur : (uint32_t)(da < (int64_t)ws.cap ? da : ws.cap);
+            if (ws.cap > 0 && (reuse || da <= (int64_t)ws.cap)) {
+                const int32_t *src = reuse ? ws.xs[cur] : g.cols + a_start;
+                const int tau_n = reuse ? 0 : i;
+                int nxt = reuse ? 1 - cur : 0;
+                uint32_t n = n_src;
+                uint64_t Wl = 0;
+                const int passes = reuse ? 1 : (n_other > 0 ? n_other : 1);
+                for (int pss = 0; pss < passes; ++pss) {
+                    const int32_t *R = nullptr;
+                    int64_t m = 0;
+                    if (reuse) {
+                        const int32_t u = tau_s[i - 1];
+                        R = g.cols + __ldg(g.off + u);
+                        m = __ldg(g.off + u + 1) - __ldg(g.off + u);
+                    } else if (n_other > 0) {
+                        R = g.cols + o_start[pss];
+                        m = o_len[pss];
+                    }
+                    if (pss == passes - 1) {
+                        n = filter_list<true>(src, n, R, m, tau_s, pss == 0 ? tau_n : 0, ws.xs[nxt], ws.pw[nxt],
+                                              S.q, S.approx != 0, &Wl, lane);
+                    } else {
+                        n = filter_list<false>(src, n, R, m, tau_s, pss == 0 ? tau_n : 0, ws.xs[nxt], nullptr,
+                                               S.q, S.approx != 0, nullptr, lane);
+                        src = ws.xs[nxt];
+                        nxt = 1 - nxt;
+                    }
+                }
+                __syncwarp();
+                if (S.approx && S.nb > 1) sec += n;
+                W = Wl;
+                cur = nxt;
+                n_cur = n;
+                if (W == 0) { out.sectors = sec; return out; }
+                const uint64_t r = draw_below(W, t, (uint64_t)(i + 1), kStreamTrial, Q.seed);
+                const int64_t j = warp_find(ws.pw[cur], n, r, 0u, 0, 0, lane);
+                v = ws.xs[cur][j];
+                qv = ws.pw[cur][j] - (j > 0 ? ws.pw[cur][j - 1] : 0);
+                X = X * ((double)W / (double)qv);
+                __syncwarp();
+                if (lane == 0) tau_s[i] = v;
+                __syncwarp();
+                continue;
+            }
+            cur = -1;
+            const int64_t nwin = (da + 31) >> 5;
+            const int64_t bsz = (nwin + 31) >> 5;              // windows per bucket
+            uint64_t running = 0, bucket_end = 0, nsurv = 0;
+            // last window kept in registers (most rows need a single window)
+            uint64_t last_before = 0, last_incl = 0, last_w = 0;
+            int32_t last_x = -1;
+            for (int64_t w = 0; w < nwin; ++w) {
+                bool ok;
+                int32_t x;
+                const uint64_t wt = window_weight(g, S, tau_s, i, a_start, da, w * 32 + lane, o_start,
+                                                  o_len, n_other, ok, x);
+                nsurv += __popc(__ballot_sync(kFull, ok));
+                const uint64_t incl = warp_incl_scan(wt, lane);
+                const uint64_t wtot = __shfl_sync(kFull, incl, 31);
+                last_before = running;
+                last_incl = incl;
+                last_w = wt;
+                last_x = x;
+                running += wtot;
+                if ((w + 1) % bsz == 0 || w == nwin - 1) {
+                    if (lane == (int)(w / bsz)) bucket_end = running;
+                }
+            }
+            if (S.approx && S.nb > 1) sec += nsurv;
+            W = running;
+            if (W == 0) { out.sectors = sec; return out; }
+            const uint64_t r = draw_below(W, t, (uint64_t)(i + 1), kStreamTrial, Q.seed);
+            if (r >= last_before) {
+                const bool hit = last_w > 0 && last_before + last_incl > r;
+                const int src = __ffs(__ballot_sync(kFull, hit)) - 1;
+                v = __shfl_sync(kFull, last_x, src);
+                qv = __shfl_sync(kFull, last_w, src);
+            } else {
+                const int64_t nbuck = (nwin + bsz - 1) / bsz;
+                const int b = __ffs(__ballot_sync(kFull, lane < nbuck && bucket_end > r)) - 1;
+                const uint64_t prev = __shfl_sync(kFull, bucket_end, b > 0 ? b - 1 : 0);
+                uint64_t run2 = b > 0 ? prev : 0;
+                const int64_t w_end = (b + 1) * bsz < nwin ? (b + 1) * bsz : nwin;
+                for (int64_t w = (int64_t)b * bsz; w < w_end; ++w) {
+                    bool ok;
+                    int32_t x;
+                    const uint64_t wt = window_weight(g, S, tau_s, i, a_start, da, w * 32 + lane,
+                                                      o_start, o_len, n_other, ok, x);
+                    const uint64_t incl = warp_incl_scan(wt, lane);
+                    const uint64_t wtot = __shfl_sync(kFull, incl, 31);
+                    if (run2 + wtot > r) {
+                        const bool hit = wt > 0 && run2 + incl > r;
+                        const int src = __ffs(__ballot_sync(kFull, hit)) - 1;
+                        v = __shfl_sync(kFull, x, src);
+                        qv = __shfl_sync(kFull, wt, src);
+                        break;
+                    }
+                    run2 += wtot;
+                }
+            }
+        }
+        X = X * ((double)W / (double)qv);
+        __syncwarp();
+        if (lane == 0) tau_s[i] = v;
+        __syncwarp();
+    }
+    out.x = X;
+    out.hit = 1;
+    out.sectors = sec;
+    return out;
+}
+
+// Work items come from `items`, or, when it is null, are implicit: item j covers
+// trials [implicit_first + 1024 j, ...) of query 0 up to implicit_count trials and
+// writes slot j.  n_items_ptr[0] holds the number of items.
+template <bool kDump>
+__global__ void __launch_bounds__(kBlock) sample_kernel(GraphView g, const DevQuery *__restrict__ queries,
+                                                        const WorkItem *__restrict__ items,
+                                                        const uint32_t *__restrict__ n_items_ptr,
+                                                        uint32_t *counter, uint64_t *tile_out,
+                                                        DumpView dump, uint64_t implicit_first,
+                                                        uint64_t implicit_count, char *scratch,
+                                                        uint32_t scratch_cap)
+{
+    __shared__ DevQuery sq;
+    __shared__ double xs[kTile];
+    __shared__ double red[kBlock];
+    __shared__ double red2[kBlock];
+    __shared__ int32_t tau_s[kWarps][kMaxK];
+    __shared__ uint32_t s_item, s_next, s_hits;
+    __shared__ unsigned long long s_sec;
+    __shared__ int s_query, s_reload;
+    __shared__ WorkItem s_it;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t n_items = *n_items_ptr;
+    WarpSets ws;
+    {
+        const size_t per = (size_t)scratch_cap * 2 * (sizeof(int32_t) + sizeof(uint64_t));
+        const size_t stride = (per + 255) / 256 * 256;
+        char *base = scratch + stride * ((size_t)blockIdx.x * kWarps + warp);
+        ws.cap = scratch ? scratch_cap : 0;
+        ws.xs[0] = (int32_t *)base;
+        ws.xs[1] = ws.xs[0] + scratch_cap;
+        ws.pw[0] = (uint64_t *)(base + (size_t)scratch_cap * 2 * sizeof(int32_t));
+        ws.pw[1] = ws.pw[0] + scratch_cap;
+    }
+    if (threadIdx.x == 0) s_query = -1;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const uint32_t id = atomicAdd(counter, 1u);
+            s_item = id;
+            if (id < n_items) {
+                WorkItem w;
+                if (items) {
+                    w = items[id];
+                } else {
+                    const uint64_t done = (uint64_t)id * kTile;
+                    const uint64_t left = implicit_count - done;
+                    w.query = 0;
+                    w.count = (uint32_t)(left < (uint64_t)kTile ? left : (uint64_t)kTile);
+                    w.first = implicit_first + done;
+                    w.slot = id;
+                }
+                s_it = w;
+                s_reload = (int)w.query != s_query;
+                s_query = (int)w.query;
+            }
+            s_next = 0;
+            s_hits = 0;
+            s_sec = 0;
+        }
+        __syncthreads();
+        if (s_item >= n_items) break;
+        const WorkItem it = s_it;
+        if (s_reload) {
+            // stage the query description in shared memory
+            const int words = (int)(sizeof(DevQuery) / sizeof(uint32_t));
+            const uint32_t *src = (const uint32_t *)(queries + it.query);
+            uint32_t *dst = (uint32_t *)&sq;
+            for (int j = threadIdx.x; j < words; j += kBlock) dst[j] = src[j];
+        }
+        for (int j = threadIdx.x; j < kTile; j += kBlock) xs[j] = 0.0;
+        __syncthreads();
+        for (;;) {
+            uint32_t tt = 0;
+            if (lane == 0) tt = atomicAdd(&s_next, 1u);
+            tt = __shfl_sync(kFull, tt, 0);
+            if (tt >= it.count) break;
+            const uint64_t t = it.first + tt;
+            const TrialOut r = run_trial(g, sq, t, tau_s[warp], ws, lane);
+            if (lane == 0) {
+                xs[tt] = r.x;
+                if (r.hit) atomicAdd(&s_hits, 1u);
+                atomicAdd(&s_sec, (unsigned long long)r.sectors);
+                if (kDump) {
+                    const uint64_t d = t - dump.first;
+                    if (dump.hit) dump.hit[d] = (uint8_t)r.hit;
+                    if (dump.x) dump.x[d] = r.x;
+                    if (dump.sectors) dump.sectors[d] = r.sectors;
+                }
+            }
+            if (kDump && dump.emb && lane < kMaxK) dump.emb[(t - dump.first) * kMaxK + lane] = tau_s[warp][lane];
+            __syncwarp();
+        }
+        __syncthreads();
+        // fixed-order reduction of the tile: strided partial sums, then a tree
+        {
+            double s = 0.0, s2 = 0.0;
+            for (int j = threadIdx.x; j < kTile; j += kBlock) {
+                const double x = xs[j];
+                s += x;
+                s2 += x * x;
+            }
+            red[threadIdx.x] = s;
+            red2[threadIdx.x] = s2;
+        }
+        __syncthreads();
+        for (int w = kBlock / 2; w > 0; w >>= 1) {
+            if (threadIdx.x < w) {
+                red[threadIdx.x] += red[threadIdx.x + w];
+                red2[threadIdx.x] += red2[threadIdx.x + w];
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            uint64_t *o = tile_out + 4 * it.slot;
+            o[0] = s_hits;
+            o[1] = s_sec;
+            o[2] = (uint64_t)__double_as_longlong(red[0]);
+            o[3] = (uint64_t)__double_as_longlong(red2[0]);
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+int sampler_occupancy(int *blocks_per_sm)
+{
+    return cuda_status(cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, sample_kernel<false>,
+                                                                    kBlock, 0));
+}
+
+// Enqueue one sampler launch over lb's staged queries and items (already on the
+// device; lb.d_counter[0] zeroed and lb.d_counter[1] = number of items).  With
+// implicit_count > 0 the items are implicit tiles of query 0 (see the kernel).
+int launch_sampler(agis_graph *g, LaunchBuffers &lb, int grid, const DumpView *dump,
+                   cudaStream_t stream, uint64_t implicit_first, uint64_t implicit_count,
+                   uint64_t *tile_out)
+{
+    GraphView gv{g->off, g->cols, g->nv, g->nnz};
+    const WorkItem *items = implicit_count ? nullptr : lb.d_items;
+    uint64_t *out = tile_out ? tile_out : lb.d_out;
+    if (dump) {
+        count_launch();
+        sample_kernel<true><<<grid, kBlock, 0, stream>>>(gv, lb.d_queries, items, lb.d_counter + 1,
+                                                         lb.d_counter, out, *dump, implicit_first,
+                                                         implicit_count, (char *)lb.d_scratch, lb.scratch_cap);
+    } else {
+        DumpView none{nullptr, nullptr, nullptr, nullptr, 0};
+        count_launch();
+        sample_kernel<false><<<grid, kBlock, 0, stream>>>(gv, lb.d_queries, items, lb.d_counter + 1,
+                                                          lb.d_counter, out, none, implicit_first,
+                                                          implicit_count, (char *)lb.d_scratch, lb.scratch_cap);
+    }
+    return cuda_status(cudaGetLastError());
+}
+
+// Adds the sampler as a kernel node of a CUDA graph (explicit items, no dump).
+int add_sampler_node(agis_graph *g, LaunchBuffers &lb, int grid, cudaGraph_t graph,
+                     const cudaGraphNode_t *deps, size_t ndeps, cudaGraphNode_t *node)
+{
+    static GraphView gv;
+    static DumpView none;
+    static const DevQuery *q;
+    static const WorkItem *it;
+    static const uint32_t *nptr;
+    static uint32_t *ctr;
+    static uint64_t *out;
+    static uint64_t z0, z1;
+    static char *scr;
+    static uint32_t cap;
+    gv = GraphView{g->off, g->cols, g->nv, g->nnz};
+    none = DumpView{nullptr, nullptr, nullptr, nullptr, 0};
+    q = lb.d_queries;
+    it = lb.d_items;
+    nptr = lb.d_counter + 1;
+    ctr = lb.d_counter;
+    out = lb.d_out;
+    z0 = z1 = 0;
+    scr = (char *)lb.d_scratch;
+    cap = lb.scratch_cap;
+    void *args[] = {&gv, &q, &it, &nptr, &ctr, &out, &none, &z0, &z1, &scr, &cap};
+    cudaKernelNodeParams p = {};
+    p.func = (void *)sample_kernel<false>;
+    p.gridDim = dim3(grid);
+    p.blockDim = dim3(kBlock);
+    p.sharedMemBytes = 0;
+    p.kernelParams = args;
+    return cuda_status(cudaGraphAddKernelNode(node, graph, deps, ndeps, &p));
+}
+
+}  // namespace agis

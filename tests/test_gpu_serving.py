@@ -1,0 +1,147 @@
+"""Batching and serving invariance (a result is the same alone, batched and served),
+memory admission of the server, and the device R-MAT generator."""
+import time
+
+import numpy as np
+import pytest
+
+from paper_2601_01388_b300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+CMIN = 2.0 ** -10
+
+
+@pytest.fixture(scope="module")
+def agis():
+    from tests.conftest import has_gpu
+    if not has_gpu():
+        pytest.skip("needs a CUDA device")
+    from paper_2601_01388_b300 import build
+    build.build()
+    from paper_2601_01388_b300 import agis as A
+    return A
+
+
+@pytest.fixture(scope="module")
+def setup(agis):
+    ctx = agis.Context(0)
+    off, cols = I.rmat_graph(12, 16, seed=3)
+    g = agis.Graph(ctx, off, cols)
+    g.preprocess(1, CMIN)
+    return ctx, g
+
+
+def wait_all(srv, tickets, timeout=300):
+    done = {}
+    t0 = time.time()
+    while len(done) < len(tickets):
+        assert time.time() - t0 < timeout, "server did not finish"
+        for t in tickets:
+            if t not in done:
+                r = srv.poll(t)
+                if r is not None:
+                    done[t] = r
+        time.sleep(0.001)
+    return [done[t] for t in tickets]
+
+
+def queries(agis, n=12):
+    rng = np.random.Generator(np.random.Philox(key=[5, 0]))
+    out = []
+    for i in range(n):
+        k, e = I.random_connected_pattern(rng, 3, 6, 0.3)
+        o = agis.default_opts(mode=i % 3, seed=50 + i, eps=float(0.02 + 0.03 * rng.random()), delta=0.05,
+                              chunk_trials=4096, min_trials=4096, max_trials=1 << 21)
+        out.append((agis.Pattern(k, e), o))
+    return out
+
+
+KEYS = ("trials", "hits", "sectors", "converged", "sum_x", "sum_x2", "estimate")
+
+
+def test_served_equals_alone_and_batched(agis, setup):
+    ctx, g = setup
+    qs = queries(agis)
+    alone = [agis.estimate(g, p, o) for p, o in qs]
+    batched = agis.estimate_batch(g, [p for p, _ in qs], [o for _, o in qs])
+    srv = agis.Server(g, 8 << 30, 5)
+    tickets = []
+    for j, (p, o) in enumerate(qs):             # staggered arrivals while others run
+        tickets.append(srv.submit(p, o))
+        if j % 3 == 2:
+            time.sleep(0.002)
+    served = wait_all(srv, tickets)
+    st = srv.stats()
+    srv.close()
+    for a, b, c in zip(alone, batched, served):
+        for k in KEYS:
+            assert a[k] == b[k] == c[k], k
+    assert st["completed"] == len(qs)
+    assert 1 <= st["peak_slots"] <= 5
+
+
+def test_admission_by_memory(agis, setup):
+    ctx, g = setup
+    g.drop_tables()
+    nv, nnz = g.info()["nv"], g.info()["nnz"]
+    qs = queries(agis, 6)
+    alone = [agis.estimate(g, p, o) for p, o in qs]
+    g.drop_tables()
+    # room for the largest single query's tables (q per vertex, a vertex prefix for
+    # step 1, a row prefix per single-backward f_approx step), not for all of them
+    def need(p, o):
+        info = p.info()
+        use = p.decide(o.mode, o.beta)
+        cfgs = {}
+        for i in range(info["k"]):
+            if use[i]:
+                c = cfgs.setdefault(info["cfg"][i], [False, False])
+                c[0] |= i == 0
+                c[1] |= i > 0 and len(info["back"][i]) == 1
+        return sum(8 * nv + (8 * nv if a else 0) + (8 * nnz if b else 0) for a, b in cfgs.values())
+    budget = max(need(p, o) for p, o in qs)
+    assert budget < sum(need(p, o) for p, o in qs)
+    srv = agis.Server(g, budget, 6)
+    served = wait_all(srv, [srv.submit(p, o) for p, o in qs])
+    srv.close()
+    for a, c in zip(alone, served):
+        assert a["trials"] == c["trials"] and a["sum_x"] == c["sum_x"]
+
+
+def test_query_that_cannot_fit_fails_cleanly(agis, setup):
+    ctx, g = setup
+    g.drop_tables()
+    srv = agis.Server(g, 1024, 2)
+    p = agis.Pattern(*I.PATTERNS["4-clique"])
+    t = srv.submit(p, agis.default_opts(mode=1, max_trials=1 << 16))
+    t0 = time.time()
+    while True:
+        try:
+            r = srv.poll(t)
+        except agis.AgisError as e:
+            assert e.status == agis.ERR_NOMEM
+            break
+        assert r is None and time.time() - t0 < 60
+        time.sleep(0.001)
+    srv.close()
+
+
+def test_device_rmat_is_a_valid_graph(agis):
+    ctx = agis.Context(0)
+    g = agis.Graph.rmat(ctx, 14, 16, 0.57, 0.19, 0.19, seed=1)
+    g.validate()
+    info = g.info()
+    off, cols = g.csr()
+    assert info["nv"] == 1 << 14 and len(cols) == info["nnz"] == off[-1]
+    deg = np.diff(off)
+    assert deg.max() == info["max_degree"]
+    # same shape as the host generator's graph (different random streams)
+    hoff, hcols = I.rmat_graph(14, 16, seed=1)
+    assert abs(len(cols) - len(hcols)) / len(hcols) < 0.03
+    assert 0.5 < deg.max() / np.diff(hoff).max() < 2.0
+    g2 = agis.Graph.rmat(ctx, 14, 16, 0.57, 0.19, 0.19, seed=1)
+    o2, c2 = g2.csr()
+    assert (o2 == off).all() and (c2 == cols).all()          # reproducible
+    g.preprocess(1, CMIN)
+    r = agis.estimate(g, agis.Pattern(*I.PATTERNS["triangle"]), agis.default_opts(eps=0.0, max_trials=1 << 16))
+    assert r["hits"] > 0
