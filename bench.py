@@ -56,6 +56,9 @@ def parse_args():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--json-out", default="")
+    ap.add_argument("--serve-load", type=float, default=0.0,
+                    help="also run a Poisson serving load at this many queries/s for --serve-seconds")
+    ap.add_argument("--serve-seconds", type=float, default=20.0)
     return ap.parse_args()
 
 
@@ -281,6 +284,47 @@ def cpu_rate(pool, names, seconds):
     return n / dt, n, dt, per
 
 
+# ------------------------------------------------------------------ serving load
+
+def serve_load(agis, g, rate_qps, seconds, seed=7, max_slots=64, budget=200 << 30):
+    """Poisson arrivals of random connected 3-8-vertex patterns (Pruefer tree plus
+    extra edges at p = 0.3) with target relative error uniform in [1%, 5%] at 95%
+    confidence; returns latency percentiles and throughput."""
+    from paper_2601_01388_b300 import inputs as I
+    rng = np.random.Generator(np.random.Philox(key=[seed, 0x5345]))
+    n = max(1, int(rate_qps * seconds))
+    arrivals = np.cumsum(rng.exponential(1.0 / rate_qps, size=n))
+    qs = []
+    for i in range(n):
+        k, e = I.random_connected_pattern(rng, 3, 8, 0.3)
+        o = agis.default_opts(mode=0, seed=1000 + i, eps=float(rng.uniform(0.01, 0.05)), delta=0.05,
+                              chunk_trials=1 << 16, min_trials=1 << 16, max_trials=1 << 26)
+        qs.append((agis.Pattern(k, e), o))
+    srv = agis.Server(g, budget, max_slots)
+    t0 = time.perf_counter()
+    pending, lat, conv = {}, [], 0
+    i = 0
+    while i < n or pending:
+        now = time.perf_counter() - t0
+        while i < n and arrivals[i] <= now:
+            pending[srv.submit(*qs[i])] = i
+            i += 1
+        for tk in list(pending):
+            r = srv.poll(tk)
+            if r is not None:
+                lat.append(r["latency_s"])
+                conv += r["converged"]
+                del pending[tk]
+        time.sleep(0.0002)
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    lat = np.array(lat)
+    return {"rate_qps": rate_qps, "queries": n, "wall_s": wall, "qps": n / wall,
+            "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "converged": int(conv), "epochs": st["epochs"], "peak_slots": st["peak_slots"]}
+
+
 # ------------------------------------------------------------------ GPU arm
 
 def run_gpu(args, world, rank, local):
@@ -439,6 +483,10 @@ def run_gpu(args, world, rank, local):
                             "converged": r["converged"]})
             tte["uniform_plain"] = uni
 
+        serving = None
+        if args.serve_load > 0:
+            serving = serve_load(agis, g, args.serve_load, args.serve_seconds)
+
     cpu = None
     if pool is not None:
         t_prep = pool.preprocess()
@@ -472,6 +520,8 @@ def run_gpu(args, world, rank, local):
         "per_pattern": per_pattern,
         "time_to_1pct": tte,
     }
+    if serving is not None:
+        line["serving"] = serving
     return line
 
 

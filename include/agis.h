@@ -217,6 +217,15 @@ int agis_dump_trials(agis_graph *g, const agis_pattern *p, const agis_opts *opts
 int agis_sample_device(agis_graph *g, const agis_pattern *p, const agis_opts *opts,
                        uint64_t first, uint64_t ntiles, uint64_t *tile_out);
 
+/* agis_autotune: picks the sampler's persistent grid for this graph and query mix
+ * -- resident CTAs per SM, 1 up to the occupancy limit -- by timing a fixed budget
+ * of trials_per_query trials of every query at each setting (CUDA events on the
+ * context's stream), and keeps the fastest in the context for later launches.
+ * Results never depend on the setting (tiles and their sums are fixed).
+ * *blocks_per_sm (may be NULL) receives the choice.  Errors: ARG, STATE, NOMEM, CUDA. */
+int agis_autotune(agis_graph *g, int n, const agis_pattern *const *patterns, const agis_opts *opts,
+                  uint64_t trials_per_query, int32_t *blocks_per_sm);
+
 /* agis_prepare: builds, for the query's f_approx steps, the quantised weight tables
  * of Eq. probability_function and their prefix sums (Sec. 4.4 / Sec. 5.1: f_approx
  * needs the per-vertex weights of every candidate); later calls reuse them.  Blocks

@@ -31,7 +31,7 @@ EXPORTS = [
     "agis_graph_preprocess", "agis_graph_info", "agis_graph_stats_copy", "agis_graph_weight_table",
     "agis_graph_row_prefix", "agis_graph_validate", "agis_graph_copy_csr", "agis_graph_drop_tables", "agis_graph_free", "agis_graph_generate_rmat",
     "agis_pattern_create", "agis_pattern_info", "agis_pattern_decide", "agis_pattern_free",
-    "agis_estimate", "agis_estimate_batch", "agis_dump_trials", "agis_sample_device",
+    "agis_estimate", "agis_estimate_batch", "agis_autotune", "agis_dump_trials", "agis_sample_device",
     "agis_prepare", "agis_z_of_delta", "agis_kernel_launches", "agis_server_create", "agis_server_submit", "agis_server_poll",
     "agis_server_stats", "agis_server_destroy",
 ]
@@ -82,6 +82,7 @@ _sig = {
     "agis_dump_trials": ([VP, VP, P(Opts), C.c_uint64, C.c_uint64, VP, VP, VP, VP], C.c_int),
     "agis_sample_device": ([VP, VP, P(Opts), C.c_uint64, C.c_uint64, VP], C.c_int),
     "agis_prepare": ([VP, VP, P(Opts)], C.c_int),
+    "agis_autotune": ([VP, C.c_int, P(VP), P(Opts), C.c_uint64, P(C.c_int32)], C.c_int),
     "agis_z_of_delta": ([C.c_double], C.c_double),
     "agis_kernel_launches": ([], C.c_uint64),
     "agis_server_create": ([VP, C.c_size_t, C.c_int, P(VP)], C.c_int),
@@ -311,6 +312,15 @@ def dump_trials(graph: Graph, pattern: Pattern, opts: Opts, first: int, count: i
     _check(_lib.agis_dump_trials(graph.h, pattern.h, C.byref(opts), first, count, _ptr(emb), _ptr(hit),
                                  _ptr(x), _ptr(sec)), "agis_dump_trials")
     return emb, hit, x, sec
+
+
+def autotune(graph: Graph, patterns, opts_list, trials_per_query=1 << 16) -> int:
+    n = len(patterns)
+    ph = (VP * n)(*[p.h for p in patterns])
+    oa = (Opts * n)(*opts_list)
+    b = C.c_int32()
+    _check(_lib.agis_autotune(graph.h, n, ph, oa, trials_per_query, C.byref(b)), "agis_autotune")
+    return b.value
 
 
 def prepare(graph: Graph, pattern: Pattern, opts: Opts):

@@ -66,6 +66,9 @@ struct GraphView {
     const int32_t *cols;
     int64_t nv;
     int64_t nnz;
+    const int32_t *hub_id;      // per vertex: index of its neighbour bitmap, -1 if none
+    const uint32_t *hub_bits;   // bitmaps, hub_words 32-bit words each
+    int64_t hub_words;
 };
 
 struct WeightTable {
@@ -112,6 +115,7 @@ struct LaunchBuffers {
 }  // namespace agis
 
 struct agis_ctx {
+    std::atomic<int> refs{1};   // the creator plus every live graph of this context
     int device = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
@@ -130,6 +134,7 @@ struct agis_pattern {
 };
 
 struct agis_graph {
+    std::atomic<int> refs{1};   // the creator plus every live server on this graph
     agis_ctx *ctx = nullptr;
     int64_t nv = 0, nnz = 0, max_deg = 0;
     int64_t *off = nullptr;
@@ -144,11 +149,18 @@ struct agis_graph {
     std::recursive_mutex mu;
     agis::LaunchBuffers lb;     // used by estimate/batch/dump (under mu)
     size_t rowp_budget = 0;     // largest row-prefix table built (bytes); beyond it draws scan rows
+    // neighbour bitmaps of the highest-degree vertices (built by preprocessing)
+    int32_t *hub_id = nullptr;
+    uint32_t *hub_bits = nullptr;
+    int64_t hub_words = 0;
+    int64_t n_hubs = 0;
+    int64_t hub_min_degree = 0;
 };
 
 namespace agis {
 
 // graph.cu
+int build_hub_bitmaps(agis_graph *g);
 int build_weight_table(agis_graph *g, const int32_t cfg[4], bool need_pref, bool need_rowp,
                        WeightTable **out);
 uint64_t cfg_key(const int32_t cfg[4]);
@@ -200,6 +212,13 @@ int run_epoch_graph(agis_graph *g, std::vector<QueryRun *> &runs, const std::vec
 double now_s();
 
 inline int cuda_status(cudaError_t e) { return e == cudaSuccess ? AGIS_OK : AGIS_ERR_CUDA; }
+
+// Lifetimes: a graph keeps its context alive and a server its graph, whatever
+// order the caller releases them in.
+void ctx_retain(agis_ctx *c);
+void ctx_release(agis_ctx *c);
+void graph_retain(agis_graph *g);
+void graph_release(agis_graph *g);
 
 // process-wide count of kernel launches (diagnostics)
 extern std::atomic<uint64_t> g_launches;

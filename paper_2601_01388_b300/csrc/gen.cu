@@ -243,6 +243,7 @@ extern "C" int agis_graph_generate_rmat(agis_ctx *ctx, int scale, int edge_facto
         for (uint64_t v = 0; v < nv; ++v) m = std::max(m, h[v + 1] - h[v]);
         g->max_deg = m;
     }
+    ctx_retain(ctx);
     *out = g;
     return AGIS_OK;
 }

@@ -3,6 +3,7 @@
 // tables of Eq. probability_function with their prefix sums.
 #include <algorithm>
 #include <cmath>
+#include <functional>
 #include <cstring>
 #include <new>
 
@@ -103,6 +104,18 @@ __global__ void k_cluster_hits(const int64_t *off, const int32_t *cols, int64_t 
         }
         for (int o = 16; o > 0; o >>= 1) h += __shfl_xor_sync(kFull, h, o);
         if (lane == 0) hits[v] = h;
+    }
+}
+
+// Neighbour bitmap of hub h (one CTA per hub): bit x set iff x is a neighbour.
+__global__ void k_hub_bitmaps(const int64_t *off, const int32_t *cols, const int32_t *hubs,
+                              int64_t words, uint32_t *bits)
+{
+    const int32_t v = hubs[blockIdx.x];
+    uint32_t *bm = bits + (int64_t)blockIdx.x * words;
+    for (int64_t e = off[v] + threadIdx.x; e < off[v + 1]; e += blockDim.x) {
+        const int32_t x = cols[e];
+        atomicOr(bm + (x >> 5), 1u << (x & 31));
     }
 }
 
@@ -300,6 +313,59 @@ int inclusive_scan(agis_graph *g, const uint64_t *in, int64_t n, uint64_t *out)
 
 }  // namespace
 
+// Bitmaps for every vertex of degree >= max(1024, t), t the smallest degree whose
+// hub set fits a sixteenth of device memory (nv bits per hub).  A membership test
+// against such a row is then one independent load.
+int build_hub_bitmaps(agis_graph *g)
+{
+    cudaStream_t st = g->ctx->stream;
+    cudaFree(g->hub_id);
+    cudaFree(g->hub_bits);
+    g->hub_id = nullptr;
+    g->hub_bits = nullptr;
+    g->n_hubs = 0;
+    g->hub_words = (g->nv + 31) / 32;
+    std::vector<int64_t> off((size_t)g->nv + 1);
+    AGIS_CUDA_TRY(cudaMemcpy(off.data(), g->off, sizeof(int64_t) * off.size(), cudaMemcpyDeviceToHost));
+    std::vector<int64_t> deg((size_t)g->nv);
+    for (int64_t v = 0; v < g->nv; ++v) deg[(size_t)v] = off[(size_t)v + 1] - off[(size_t)v];
+    size_t free_b = 0, total_b = 0;
+    AGIS_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+    const size_t per_hub = sizeof(uint32_t) * (size_t)g->hub_words;
+    const size_t max_hubs = std::min<size_t>((total_b / 16) / per_hub, 1u << 20);
+    std::vector<int64_t> sorted(deg);
+    int64_t t = 1024;
+    if (sorted.size() > max_hubs && max_hubs > 0) {
+        std::nth_element(sorted.begin(), sorted.begin() + (max_hubs - 1), sorted.end(), std::greater<int64_t>());
+        t = std::max<int64_t>(t, sorted[max_hubs - 1] + 1);
+    }
+    std::vector<int32_t> hubs;
+    std::vector<int32_t> hub_id((size_t)g->nv, -1);
+    for (int64_t v = 0; v < g->nv; ++v)
+        if (deg[(size_t)v] >= t && hubs.size() < max_hubs) {
+            hub_id[(size_t)v] = (int32_t)hubs.size();
+            hubs.push_back((int32_t)v);
+        }
+    g->hub_min_degree = t;
+    AGIS_CUDA_TRY(cudaMalloc(&g->hub_id, sizeof(int32_t) * (size_t)g->nv));
+    AGIS_CUDA_TRY(cudaMemcpyAsync(g->hub_id, hub_id.data(), sizeof(int32_t) * (size_t)g->nv, cudaMemcpyHostToDevice, st));
+    if (!hubs.empty()) {
+        AGIS_CUDA_TRY(cudaMalloc(&g->hub_bits, per_hub * hubs.size()));
+        AGIS_CUDA_TRY(cudaMemsetAsync(g->hub_bits, 0, per_hub * hubs.size(), st));
+        int32_t *d_hubs = nullptr;
+        AGIS_CUDA_TRY(cudaMallocAsync(&d_hubs, sizeof(int32_t) * hubs.size(), st));
+        AGIS_CUDA_TRY(cudaMemcpyAsync(d_hubs, hubs.data(), sizeof(int32_t) * hubs.size(), cudaMemcpyHostToDevice, st));
+        count_launch();
+        k_hub_bitmaps<<<(unsigned)hubs.size(), 256, 0, st>>>(g->off, g->cols, d_hubs, g->hub_words, g->hub_bits);
+        AGIS_CUDA_TRY(cudaGetLastError());
+        cudaFreeAsync(d_hubs, st);
+    }
+    AGIS_CUDA_TRY(cudaStreamSynchronize(st));
+    g->n_hubs = (int64_t)hubs.size();
+    g->lb.generation++;          // a captured epoch graph holds the old bitmap addresses
+    return AGIS_OK;
+}
+
 uint64_t cfg_key(const int32_t cfg[4])
 {
     return ((uint64_t)(uint8_t)cfg[0] << 24) | ((uint64_t)(uint8_t)cfg[1] << 16) |
@@ -467,6 +533,7 @@ extern "C" int agis_graph_load_csr(agis_ctx *ctx, const void *offsets, int offse
         for (int64_t v = 0; v < nv; ++v) m = std::max(m, h[(size_t)v + 1] - h[(size_t)v]);
         g->max_deg = m;
     }
+    ctx_retain(ctx);
     *out = g;
     return AGIS_OK;
 }
@@ -488,6 +555,8 @@ extern "C" int agis_graph_preprocess(agis_graph *g, uint64_t seed, double c_min)
     k_cluster_hits<<<blocks, 256, 0, st>>>(g->off, g->cols, g->nv, seed, g->hits);
     AGIS_CUDA_TRY(cudaGetLastError());
     AGIS_CUDA_TRY(cudaStreamSynchronize(st));
+    int rc = build_hub_bitmaps(g);
+    if (rc != AGIS_OK) return rc;
     g->prepped = true;
     g->c_min = c_min;
     g->prep_seed = seed;

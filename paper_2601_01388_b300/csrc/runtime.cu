@@ -130,15 +130,15 @@ size_t scratch_stride(uint32_t cap)
 }
 
 // Per-warp candidate-list scratch for a launch of `grid` CTAs: lists as long as
-// the largest row when that fits in an eighth of device memory (longer anchor
-// rows then take the sampler's list-free path).
+// the largest row, at most 16384 entries and within an eighth of device memory
+// (longer anchor rows take the sampler's list-free path).
 int ensure_scratch(agis_graph *g, LaunchBuffers &lb, int grid)
 {
     if (lb.d_scratch && lb.scratch_grid >= grid) return AGIS_OK;
     size_t free_b = 0, total_b = 0;
     AGIS_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
     const size_t warps = (size_t)grid * kWarps;
-    uint64_t cap = (uint64_t)std::max<int64_t>(g->max_deg, 64);
+    uint64_t cap = (uint64_t)std::min<int64_t>(std::max<int64_t>(g->max_deg, 64), 16384);
     cap = (cap + 63) / 64 * 64;
     const size_t budget = total_b / 8;
     while (cap > 64 && scratch_stride((uint32_t)cap) * warps > budget) cap = (cap / 2 + 63) / 64 * 64;
@@ -509,22 +509,28 @@ extern "C" int agis_create(int device, void *cuda_stream, agis_ctx **out)
     return AGIS_OK;
 }
 
-extern "C" int agis_destroy(agis_ctx *c)
+namespace agis {
+
+void ctx_retain(agis_ctx *c) { c->refs.fetch_add(1); }
+
+void ctx_release(agis_ctx *c)
 {
-    if (!c) return AGIS_ERR_ARG;
+    if (c->refs.fetch_sub(1) != 1) return;
     cudaSetDevice(c->device);
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
-    return AGIS_OK;
 }
 
-extern "C" int agis_graph_free(agis_graph *g)
+void graph_retain(agis_graph *g) { g->refs.fetch_add(1); }
+
+void graph_release(agis_graph *g)
 {
-    if (!g) return AGIS_ERR_ARG;
+    if (g->refs.fetch_sub(1) != 1) return;
+    agis_ctx *c = g->ctx;
     {
         std::lock_guard<std::recursive_mutex> lk(g->mu);
-        cudaSetDevice(g->ctx->device);
-        cudaStreamSynchronize(g->ctx->stream);
+        cudaSetDevice(c->device);
+        cudaStreamSynchronize(c->stream);
         for (auto &kv : g->tables) free_table(kv.second);
         g->tables.clear();
         free_buffers(g->lb);
@@ -532,8 +538,28 @@ extern "C" int agis_graph_free(agis_graph *g)
         cudaFree(g->cols);
         cudaFree(g->nsum);
         cudaFree(g->hits);
+        cudaFree(g->hub_id);
+        cudaFree(g->hub_bits);
     }
     delete g;
+    ctx_release(c);
+}
+
+}  // namespace agis
+
+// Releases the caller's reference; the context goes away once its last graph does.
+extern "C" int agis_destroy(agis_ctx *c)
+{
+    if (!c) return AGIS_ERR_ARG;
+    ctx_release(c);
+    return AGIS_OK;
+}
+
+// Releases the caller's reference; the graph goes away once no server uses it.
+extern "C" int agis_graph_free(agis_graph *g)
+{
+    if (!g) return AGIS_ERR_ARG;
+    graph_release(g);
     return AGIS_OK;
 }
 
@@ -662,3 +688,68 @@ extern "C" int agis_prepare(agis_graph *g, const agis_pattern *p, const agis_opt
 }
 
 extern "C" uint64_t agis_kernel_launches(void) { return g_launches.load(); }
+
+extern "C" int agis_autotune(agis_graph *g, int n, const agis_pattern *const *patterns, const agis_opts *opts,
+                             uint64_t trials_per_query, int32_t *blocks_per_sm)
+{
+    if (!g || n <= 0 || !patterns || !opts || trials_per_query == 0) return AGIS_ERR_ARG;
+    std::lock_guard<std::recursive_mutex> lk(g->mu);
+    AGIS_CUDA_TRY(cudaSetDevice(g->ctx->device));
+    cudaStream_t st = g->ctx->stream;
+    int occ = 1;
+    int rc = sampler_occupancy(&occ);
+    if (rc != AGIS_OK) return rc;
+    const uint64_t ntiles = (trials_per_query + kTile - 1) / kTile;
+    std::vector<DevQuery> dqs((size_t)n);
+    for (int i = 0; i < n; ++i) {
+        if ((rc = check_opts(&opts[i])) != AGIS_OK) return rc;
+        if ((rc = make_dev_query(g, patterns[i], &opts[i], &dqs[(size_t)i], nullptr)) != AGIS_OK) return rc;
+    }
+    LaunchBuffers &lb = g->lb;
+    const size_t items = (size_t)n * ntiles;
+    if ((rc = ensure_buffers(lb, (size_t)n, items)) != AGIS_OK) return rc;
+    if ((rc = ensure_scratch(g, lb, g->ctx->sm_count * std::max(1, occ))) != AGIS_OK) return rc;
+    AGIS_CUDA_TRY(cudaStreamSynchronize(st));
+    size_t k = 0;
+    for (int i = 0; i < n; ++i) {
+        lb.h_queries[i] = dqs[(size_t)i];
+        for (uint64_t j = 0; j < ntiles; ++j, ++k) {
+            WorkItem &w = lb.h_items[k];
+            w.query = (uint32_t)i;
+            w.count = kTile;
+            w.first = j * kTile;
+            w.slot = k;
+        }
+    }
+    AGIS_CUDA_TRY(cudaMemcpyAsync(lb.d_queries, lb.h_queries, sizeof(DevQuery) * (size_t)n, cudaMemcpyHostToDevice, st));
+    AGIS_CUDA_TRY(cudaMemcpyAsync(lb.d_items, lb.h_items, sizeof(WorkItem) * items, cudaMemcpyHostToDevice, st));
+    cudaEvent_t e0, e1;
+    AGIS_CUDA_TRY(cudaEventCreate(&e0));
+    AGIS_CUDA_TRY(cudaEventCreate(&e1));
+    int best = 1;
+    float best_ms = 0.0f;
+    for (int c = 1; c <= std::max(1, occ); ++c) {
+        const int grid = (int)std::min<size_t>((size_t)g->ctx->sm_count * (size_t)c, items);
+        float ms_total = 0.0f;
+        for (int rep = 0; rep < 2; ++rep) {          // the first launch warms caches
+            const uint32_t counter[2] = {0u, (uint32_t)items};
+            cudaMemcpyAsync(lb.d_counter, counter, sizeof(counter), cudaMemcpyHostToDevice, st);
+            cudaEventRecord(e0, st);
+            rc = launch_sampler(g, lb, grid, nullptr, st, 0, 0, nullptr);
+            cudaEventRecord(e1, st);
+            if (rc != AGIS_OK) break;
+            if (cudaEventSynchronize(e1) != cudaSuccess) { rc = AGIS_ERR_CUDA; break; }
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep == 1) ms_total = ms;
+        }
+        if (rc != AGIS_OK) break;
+        if (c == 1 || ms_total < best_ms) { best_ms = ms_total; best = c; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != AGIS_OK) return rc;
+    g->ctx->blocks_per_sm = best;
+    if (blocks_per_sm) *blocks_per_sm = best;
+    return AGIS_OK;
+}

@@ -46,6 +46,19 @@ __device__ __forceinline__ uint64_t row_check_sectors(int64_t da, int64_t m)
     return merge < search ? merge : search;
 }
 
+// Neighbour bitmap of vertex u, or null when u has none.
+__device__ __forceinline__ const uint32_t *bits_of(const GraphView &g, int32_t u)
+{
+    if (!g.hub_bits) return nullptr;
+    const int32_t h = __ldg(g.hub_id + u);
+    return h < 0 ? nullptr : g.hub_bits + (int64_t)h * g.hub_words;
+}
+
+__device__ __forceinline__ bool bit_test(const uint32_t *bits, int32_t x)
+{
+    return (__ldg(bits + (x >> 5)) >> (x & 31)) & 1u;
+}
+
 // ---------------------------------------------------------------- searches
 
 // Last position with row[pos] <= x, or -1 if x is absent; the probe count depends
@@ -135,8 +148,8 @@ struct TrialOut {
 __device__ __forceinline__ uint64_t window_weight(const GraphView &g, const DevStep &S,
                                                   const int32_t *tau_s, int i, int64_t a_start,
                                                   int64_t da, int64_t idx, const int64_t *o_start,
-                                                  const int64_t *o_len, int n_other, bool &ok,
-                                                  int32_t &x)
+                                                  const int64_t *o_len, const uint32_t *const *o_bits,
+                                                  int n_other, bool &ok, int32_t &x)
 {
     ok = idx < da;
     x = ok ? __ldg(g.cols + a_start + idx) : -1;
@@ -144,7 +157,7 @@ __device__ __forceinline__ uint64_t window_weight(const GraphView &g, const DevS
         for (int j = 0; j < i; ++j) ok &= (x != tau_s[j]);
     }
     for (int o = 0; o < n_other; ++o) {
-        if (ok) ok = row_find(g.cols + o_start[o], o_len[o], x) >= 0;
+        if (ok) ok = o_bits[o] ? bit_test(o_bits[o], x) : row_find(g.cols + o_start[o], o_len[o], x) >= 0;
     }
     if (!ok) return 0;
     return S.approx ? __ldg(S.q + x) : 1u;
@@ -164,25 +177,75 @@ struct WarpSets {
 // weights (q[x] under f_approx, 1 under f_uniform) are accumulated into out_pw as
 // inclusive running sums and *W receives the total.
 //
-// Membership in R is found either by a warp merge (R read once, 32 entries per
+// Membership in R is a bit test when R's vertex has a neighbour bitmap (Rbits);
+// otherwise it is found either by a warp merge (R read once, 32 entries per
 // coalesced load, each loaded entry located among the 32 list entries of the window
 // by a shuffle search) or by one binary search per list entry, whichever the sizes
 // make cheaper.
+// Appends this window's survivors (ok) to out, in lane order, with their running
+// weights when kWeigh; cnt and carry advance.
+template <bool kWeigh>
+__device__ __forceinline__ void emit_window(bool ok, int32_t x, uint64_t w, int32_t *out, uint64_t *out_pw,
+                                            uint32_t &cnt, uint64_t &carry, int lane)
+{
+    const uint32_t bal = __ballot_sync(kFull, ok);
+    const uint32_t pos = cnt + __popc(bal & ((1u << lane) - 1u));
+    if (ok) out[pos] = x;
+    if (kWeigh) {
+        const uint64_t incl = warp_incl_scan(ok ? w : 0u, lane);
+        if (ok) out_pw[pos] = carry + incl;
+        carry += __shfl_sync(kFull, incl, 31);
+    }
+    cnt += __popc(bal);
+}
+
+// Keeps the entries of the ascending list L[0, n) that are not trajectory members
+// (tau_s[0, tau_n)) and that occur in the ascending row R[0, m) (all of them when R
+// is null); survivors are appended, in order, to out.  With kWeigh the survivors'
+// weights (q[x] under f_approx, 1 under f_uniform) are accumulated into out_pw as
+// inclusive running sums and *W receives the total.
+//
+// Membership in R is a bit test when R's vertex has a neighbour bitmap (Rbits);
+// otherwise it is found either by a warp merge (R read once, 32 entries per
+// coalesced load, each loaded entry located among the 32 list entries of the window
+// by a shuffle search) or by one binary search per list entry, whichever the sizes
+// make cheaper.  The bitmap and no-row cases run four windows at a time so that
+// four list loads, four bit tests and four weight gathers are in flight together.
 template <bool kWeigh>
 __device__ uint32_t filter_list(const int32_t *L, uint32_t n, const int32_t *R, int64_t m,
-                                const int32_t *tau_s, int tau_n, int32_t *out, uint64_t *out_pw,
-                                const uint64_t *q, bool approx, uint64_t *W, int lane)
+                                const uint32_t *Rbits, const int32_t *tau_s, int tau_n, int32_t *out,
+                                uint64_t *out_pw, const uint64_t *q, bool approx, uint64_t *W, int lane)
 {
-    bool merge = false;
-    if (R) {
-        int lg = 1;
-        while ((1ll << lg) < m + 1) ++lg;
-        const int64_t merge_loads = ((int64_t)n + m + 31) / 32;
-        const int64_t search_loads = (((int64_t)n + 31) / 32) * lg;
-        merge = merge_loads <= search_loads;
-    }
     uint32_t cnt = 0;
     uint64_t carry = 0;
+    if (Rbits || !R) {
+        constexpr int U = 4;
+        for (uint32_t base = 0; base < n; base += 32 * U) {
+            int32_t x[U];
+            bool ok[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const uint32_t idx = base + 32 * u + lane;
+                ok[u] = idx < n;
+                x[u] = ok[u] ? L[idx] : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                for (int j = 0; j < tau_n; ++j) ok[u] = ok[u] && (x[u] != tau_s[j]);
+                if (Rbits) ok[u] = ok[u] && bit_test(Rbits, x[u]);
+            }
+            uint64_t w[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) w[u] = (kWeigh && ok[u]) ? (approx ? __ldg(q + x[u]) : 1u) : 0u;
+#pragma unroll
+            for (int u = 0; u < U; ++u) emit_window<kWeigh>(ok[u], x[u], w[u], out, out_pw, cnt, carry, lane);
+        }
+        if (kWeigh) *W = carry;
+        return cnt;
+    }
+    int lg = 1;
+    while ((1ll << lg) < m + 1) ++lg;
+    const bool merge = ((int64_t)n + m + 31) / 32 <= (((int64_t)n + 31) / 32) * lg;
     int64_t rpos = 0;
     for (uint32_t base = 0; base < n; base += 32) {
         const uint32_t idx = base + lane;
@@ -190,45 +253,35 @@ __device__ uint32_t filter_list(const int32_t *L, uint32_t n, const int32_t *R, 
         const int32_t x = valid ? L[idx] : 0x7fffffff;
         bool ok = valid;
         for (int j = 0; j < tau_n; ++j) ok &= (x != tau_s[j]);
-        if (R) {
-            if (merge) {
-                const int last = (n - base) >= 32 ? 31 : (int)(n - base - 1);
-                const int32_t x_last = __shfl_sync(kFull, x, last);
-                uint32_t found = 0;
-                for (;;) {
-                    const bool rvalid = rpos + lane < m;
-                    const int32_t rv = rvalid ? __ldg(R + rpos + lane) : 0x7fffffff;
-                    // position of rv among the window's entries (lanes 0..last, ascending)
-                    int lo = 0, len = last + 1;
-                    while (len > 1) {
-                        const int half = len >> 1;
-                        const int32_t xv = __shfl_sync(kFull, x, lo + half);
-                        if (xv <= rv) lo += half;
-                        len -= half;
-                    }
-                    const int32_t xlo = __shfl_sync(kFull, x, lo);
-                    uint32_t bit = (rvalid && xlo == rv) ? (1u << lo) : 0u;
-                    for (int o = 16; o > 0; o >>= 1) bit |= __shfl_xor_sync(kFull, bit, o);
-                    found |= bit;
-                    const int c = __popc(__ballot_sync(kFull, rvalid && rv <= x_last));
-                    rpos += c;
-                    if (c < 32) break;
+        if (merge) {
+            const int last = (n - base) >= 32 ? 31 : (int)(n - base - 1);
+            const int32_t x_last = __shfl_sync(kFull, x, last);
+            uint32_t found = 0;
+            for (;;) {
+                const bool rvalid = rpos + lane < m;
+                const int32_t rv = rvalid ? __ldg(R + rpos + lane) : 0x7fffffff;
+                // position of rv among the window's entries (lanes 0..last, ascending)
+                int lo = 0, len = last + 1;
+                while (len > 1) {
+                    const int half = len >> 1;
+                    const int32_t xv = __shfl_sync(kFull, x, lo + half);
+                    if (xv <= rv) lo += half;
+                    len -= half;
                 }
-                ok = ok && ((found >> lane) & 1u);
-            } else if (ok) {
-                ok = row_find(R, m, x) >= 0;
+                const int32_t xlo = __shfl_sync(kFull, x, lo);
+                uint32_t bit = (rvalid && xlo == rv) ? (1u << lo) : 0u;
+                for (int o = 16; o > 0; o >>= 1) bit |= __shfl_xor_sync(kFull, bit, o);
+                found |= bit;
+                const int c = __popc(__ballot_sync(kFull, rvalid && rv <= x_last));
+                rpos += c;
+                if (c < 32) break;
             }
+            ok = ok && ((found >> lane) & 1u);
+        } else if (ok) {
+            ok = row_find(R, m, x) >= 0;
         }
-        const uint32_t bal = __ballot_sync(kFull, ok);
-        const uint32_t pos = cnt + __popc(bal & ((1u << lane) - 1u));
-        if (ok) out[pos] = x;
-        if (kWeigh) {
-            const uint64_t w = ok ? (approx ? __ldg(q + x) : 1u) : 0u;
-            const uint64_t incl = warp_incl_scan(w, lane);
-            if (ok) out_pw[pos] = carry + incl;
-            carry += __shfl_sync(kFull, incl, 31);
-        }
-        cnt += __popc(bal);
+        const uint64_t w = (kWeigh && ok) ? (approx ? __ldg(q + x) : 1u) : 0u;
+        emit_window<kWeigh>(ok, x, w, out, out_pw, cnt, carry, lane);
     }
     if (kWeigh) *W = carry;
     return cnt;
@@ -270,9 +323,10 @@ __device__ TrialOut run_trial(const GraphView &g, const DevQuery &Q, uint64_t t,
             // trajectory members inside a's row (lane j checks tau_j)
             int64_t xp = -1;
             uint64_t xq = 0;
+            const uint32_t *abits = bits_of(g, a);
             if (lane < i && lane != jb) {
                 const int32_t m = tau_s[lane];
-                xp = row_find(g.cols + a_start, d, m);
+                if (!abits || bit_test(abits, m)) xp = row_find(g.cols + a_start, d, m);
                 if (xp >= 0) xq = S.approx ? __ldg(S.q + m) : 1u;
             }
             const uint32_t xmask = __ballot_sync(kFull, xp >= 0);
@@ -290,6 +344,7 @@ __device__ TrialOut run_trial(const GraphView &g, const DevQuery &Q, uint64_t t,
             // ---- several backward neighbours (or one, with no row-prefix table):
             //      intersect, anchored at the shortest row
             int64_t o_start[kMaxK - 1], o_len[kMaxK - 1];
+            const uint32_t *o_bits[kMaxK - 1];
             int ai = 0;
             int64_t a_start = 0, da = -1;
             for (int b = 0; b < S.nb; ++b) {
@@ -304,6 +359,7 @@ __device__ TrialOut run_trial(const GraphView &g, const DevQuery &Q, uint64_t t,
                 const int32_t u = tau_s[S.back[b]];
                 o_start[n_other] = __ldg(g.off + u);
                 o_len[n_other] = __ldg(g.off + u + 1) - o_start[n_other];
+                o_bits[n_other] = bits_of(g, u);
                 search_sec += row_check_sectors(da, o_len[n_other]);
                 ++n_other;
             }
@@ -326,21 +382,24 @@ __device__ TrialOut run_trial(const GraphView &g, const DevQuery &Q, uint64_t t,
                 const int passes = reuse ? 1 : (n_other > 0 ? n_other : 1);
                 for (int pss = 0; pss < passes; ++pss) {
                     const int32_t *R = nullptr;
+                    const uint32_t *Rb = nullptr;
                     int64_t m = 0;
                     if (reuse) {
                         const int32_t u = tau_s[i - 1];
                         R = g.cols + __ldg(g.off + u);
                         m = __ldg(g.off + u + 1) - __ldg(g.off + u);
+                        Rb = bits_of(g, u);
                     } else if (n_other > 0) {
                         R = g.cols + o_start[pss];
                         m = o_len[pss];
+                        Rb = o_bits[pss];
                     }
                     if (pss == passes - 1) {
-                        n = filter_list<true>(src, n, R, m, tau_s, pss == 0 ? tau_n : 0, ws.xs[nxt], ws.pw[nxt],
-                                              S.q, S.approx != 0, &Wl, lane);
+                        n = filter_list<true>(src, n, R, m, Rb, tau_s, pss == 0 ? tau_n : 0, ws.xs[nxt],
+                                              ws.pw[nxt], S.q, S.approx != 0, &Wl, lane);
                     } else {
-                        n = filter_list<false>(src, n, R, m, tau_s, pss == 0 ? tau_n : 0, ws.xs[nxt], nullptr,
-                                               S.q, S.approx != 0, nullptr, lane);
+                        n = filter_list<false>(src, n, R, m, Rb, tau_s, pss == 0 ? tau_n : 0, ws.xs[nxt],
+                                               nullptr, S.q, S.approx != 0, nullptr, lane);
                         src = ws.xs[nxt];
                         nxt = 1 - nxt;
                     }
@@ -368,21 +427,30 @@ __device__ TrialOut run_trial(const GraphView &g, const DevQuery &Q, uint64_t t,
             // last window kept in registers (most rows need a single window)
             uint64_t last_before = 0, last_incl = 0, last_w = 0;
             int32_t last_x = -1;
-            for (int64_t w = 0; w < nwin; ++w) {
-                bool ok;
-                int32_t x;
-                const uint64_t wt = window_weight(g, S, tau_s, i, a_start, da, w * 32 + lane, o_start,
-                                                  o_len, n_other, ok, x);
-                nsurv += __popc(__ballot_sync(kFull, ok));
-                const uint64_t incl = warp_incl_scan(wt, lane);
-                const uint64_t wtot = __shfl_sync(kFull, incl, 31);
-                last_before = running;
-                last_incl = incl;
-                last_w = wt;
-                last_x = x;
-                running += wtot;
-                if ((w + 1) % bsz == 0 || w == nwin - 1) {
-                    if (lane == (int)(w / bsz)) bucket_end = running;
+            constexpr int U = 4;       // windows whose loads are in flight together
+            for (int64_t w0 = 0; w0 < nwin; w0 += U) {
+                bool okv[U];
+                int32_t xv[U];
+                uint64_t wtv[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    wtv[u] = window_weight(g, S, tau_s, i, a_start, da, (w0 + u) * 32 + lane, o_start,
+                                           o_len, o_bits, n_other, okv[u], xv[u]);
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int64_t w = w0 + u;
+                    if (w >= nwin) break;
+                    nsurv += __popc(__ballot_sync(kFull, okv[u]));
+                    const uint64_t incl = warp_incl_scan(wtv[u], lane);
+                    const uint64_t wtot = __shfl_sync(kFull, incl, 31);
+                    last_before = running;
+                    last_incl = incl;
+                    last_w = wtv[u];
+                    last_x = xv[u];
+                    running += wtot;
+                    if ((w + 1) % bsz == 0 || w == nwin - 1) {
+                        if (lane == (int)(w / bsz)) bucket_end = running;
+                    }
                 }
             }
             if (S.approx && S.nb > 1) sec += nsurv;
@@ -404,7 +472,7 @@ __device__ TrialOut run_trial(const GraphView &g, const DevQuery &Q, uint64_t t,
                     bool ok;
                     int32_t x;
                     const uint64_t wt = window_weight(g, S, tau_s, i, a_start, da, w * 32 + lane,
-                                                      o_start, o_len, n_other, ok, x);
+                                                      o_start, o_len, o_bits, n_other, ok, x);
                     const uint64_t incl = warp_incl_scan(wt, lane);
                     const uint64_t wtot = __shfl_sync(kFull, incl, 31);
                     if (run2 + wtot > r) {
@@ -433,7 +501,7 @@ __device__ TrialOut run_trial(const GraphView &g, const DevQuery &Q, uint64_t t,
 // trials [implicit_first + 1024 j, ...) of query 0 up to implicit_count trials and
 // writes slot j.  n_items_ptr[0] holds the number of items.
 template <bool kDump>
-__global__ void __launch_bounds__(kBlock) sample_kernel(GraphView g, const DevQuery *__restrict__ queries,
+__global__ void __launch_bounds__(kBlock, 3) sample_kernel(GraphView g, const DevQuery *__restrict__ queries,
                                                         const WorkItem *__restrict__ items,
                                                         const uint32_t *__restrict__ n_items_ptr,
                                                         uint32_t *counter, uint64_t *tile_out,
@@ -567,7 +635,7 @@ int launch_sampler(agis_graph *g, LaunchBuffers &lb, int grid, const DumpView *d
                    cudaStream_t stream, uint64_t implicit_first, uint64_t implicit_count,
                    uint64_t *tile_out)
 {
-    GraphView gv{g->off, g->cols, g->nv, g->nnz};
+    GraphView gv{g->off, g->cols, g->nv, g->nnz, g->hub_id, g->hub_bits, g->hub_words};
     const WorkItem *items = implicit_count ? nullptr : lb.d_items;
     uint64_t *out = tile_out ? tile_out : lb.d_out;
     if (dump) {
@@ -599,7 +667,7 @@ int add_sampler_node(agis_graph *g, LaunchBuffers &lb, int grid, cudaGraph_t gra
     static uint64_t z0, z1;
     static char *scr;
     static uint32_t cap;
-    gv = GraphView{g->off, g->cols, g->nv, g->nnz};
+    gv = GraphView{g->off, g->cols, g->nv, g->nnz, g->hub_id, g->hub_bits, g->hub_words};
     none = DumpView{nullptr, nullptr, nullptr, nullptr, 0};
     q = lb.d_queries;
     it = lb.d_items;

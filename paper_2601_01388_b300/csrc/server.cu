@@ -48,28 +48,28 @@ namespace {
 
 constexpr size_t kMaxWaiting = 65536;
 
-// Device bytes a query would add: tables of its f_approx steps not yet resident.
+// Device bytes a query would add: the parts of its f_approx steps' tables that are
+// not resident yet (q per vertex; a vertex prefix for step 1; a row prefix for
+// single-backward steps while the graph's row-prefix budget allows one).
 size_t extra_bytes(agis_graph *g, const agis_pattern &p, const agis_opts &o)
 {
     uint8_t use[kMaxK];
     agis_pattern_decide(&p, o.mode, o.beta, use);
-    size_t extra = 0;
-    std::vector<uint64_t> seen;
+    std::map<uint64_t, std::pair<bool, bool>> need;   // cfg -> (vertex prefix, row prefix)
+    const bool rowp_ok = (size_t)g->nnz * sizeof(uint64_t) <= g->rowp_budget;
     for (int i = 0; i < p.k; ++i) {
         if (!use[i]) continue;
-        const bool pref = i == 0, rowp = i > 0 && p.nback[i] == 1;
-        const uint64_t key = cfg_key(p.cfg[i]);
-        auto it = g->tables.find(key);
-        const bool counted = std::find(seen.begin(), seen.end(), key) != seen.end();
-        seen.push_back(key);
-        if (it == g->tables.end()) {
-            if (!counted) extra += table_bytes(g, p.cfg[i], false, false);
-            if (pref) extra += sizeof(uint64_t) * (size_t)g->nv;
-            if (rowp) extra += sizeof(uint64_t) * (size_t)g->nnz;
-        } else {
-            if (pref && !it->second.pref) extra += sizeof(uint64_t) * (size_t)g->nv;
-            if (rowp && !it->second.rowp) extra += sizeof(uint64_t) * (size_t)g->nnz;
-        }
+        auto &f = need[cfg_key(p.cfg[i])];
+        f.first = f.first || i == 0;
+        f.second = f.second || (i > 0 && p.nback[i] == 1 && rowp_ok);
+    }
+    size_t extra = 0;
+    for (const auto &kv : need) {
+        auto it = g->tables.find(kv.first);
+        const bool have = it != g->tables.end();
+        if (!have) extra += sizeof(uint64_t) * (size_t)g->nv;
+        if (kv.second.first && !(have && it->second.pref)) extra += sizeof(uint64_t) * (size_t)g->nv;
+        if (kv.second.second && !(have && it->second.rowp)) extra += sizeof(uint64_t) * (size_t)g->nnz;
     }
     return extra;
 }
@@ -221,11 +221,13 @@ extern "C" int agis_server_create(agis_graph *g, size_t scratch_bytes, int max_s
     agis_server *s = new (std::nothrow) agis_server();
     if (!s) return AGIS_ERR_NOMEM;
     s->g = g;
+    graph_retain(g);
     s->scratch_bytes = scratch_bytes;
     s->max_slots = max_slots;
     try {
         s->worker = std::thread(scheduler, s);
     } catch (...) {
+        graph_release(g);
         delete s;
         return AGIS_ERR_NOMEM;
     }
@@ -303,6 +305,8 @@ extern "C" int agis_server_destroy(agis_server *s)
         }
     }
     for (auto &kv : s->by_ticket) delete kv.second;
+    agis_graph *g = s->g;
     delete s;
+    graph_release(g);
     return AGIS_OK;
 }
