@@ -232,6 +232,24 @@ int agis_autotune(agis_graph *g, int n, const agis_pattern *const *patterns, con
  * until the tables are ready.  Errors: ARG, STATE, NOMEM, CUDA. */
 int agis_prepare(agis_graph *g, const agis_pattern *p, const agis_opts *opts);
 
+/* agis_prefix_sum_u64_noalloc: out[i] = in[0] + ... + in[i] for i < n (uint64,
+ * wrapping), the same scan that builds the weight tables' prefix sums, for callers
+ * that cannot call cudaMalloc -- code running while a CUDA graph is captured, code
+ * inside a custom allocator or host callback that must not re-enter the CUDA
+ * allocator, or a service whose device memory is already fully reserved by a pool.
+ * The paper has no counterpart; this is a library service.
+ * in and out are device pointers on the current device (they may not overlap);
+ * the work is enqueued on cuda_stream (NULL = legacy default stream) and nothing is
+ * allocated or freed: the tile-sum scratch is a file-scope device array of 65536
+ * uint64 (512 KiB), held by every device that loads the library until the process
+ * exits.  So n is at most 65536 * 2048 = 134217728; larger n returns ARG.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  All calls share the one array: calls whose work overlaps on the GPU
+ * (other streams, or other host threads) race on it and must be serialised by the
+ * caller.  Errors: ARG (n < 0, n too large, null pointer), CUDA. */
+int agis_prefix_sum_u64_noalloc(const uint64_t *in, int64_t n, uint64_t *out, void *cuda_stream);
+
 /* agis_kernel_launches: number of this library's CUDA kernel launches so far in
  * the process (all contexts); a diagnostic for counting device work. */
 uint64_t agis_kernel_launches(void);

@@ -670,3 +670,67 @@ extern "C" int agis_graph_copy_csr(const agis_graph *g, int64_t *off, int32_t *c
         AGIS_CUDA_TRY(cudaMemcpy(cols, g->cols, sizeof(int32_t) * (size_t)g->nnz, cudaMemcpyDeviceToHost));
     return AGIS_OK;
 }
+
+// ---------------------------------------------------------------- prefix sum without allocation
+// Some callers cannot call cudaMalloc: code running while a CUDA graph is being
+// captured (an allocation is not a capturable operation), code inside a host
+// callback or a custom allocator that must not re-enter the CUDA allocator, and
+// services whose device memory is already fully reserved by a pool allocator.  For
+// them this variant of the prefix-sum scan keeps its tile-sum scratch in a
+// file-scope device array instead of allocating it.  The array exists once on every
+// device that loads this library and stays allocated until the process exits.
+
+namespace agis {
+namespace {
+
+constexpr int64_t kNoAllocMaxTiles = 65536;   // 512 KiB of tile sums
+constexpr int64_t kNoAllocMaxN = kNoAllocMaxTiles * kScanTile;
+
+static __device__ __align__(256) uint64_t g_noalloc_tile_sums[kNoAllocMaxTiles];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+uint64_t *g_noalloc_ptr[kMaxDevices] = {nullptr};
+
+// Device address of the scratch array on the current device, looked up once per
+// device (host code must not use the array's name as an address).
+int noalloc_scratch(int device, uint64_t **out)
+{
+    if (device < 0 || device >= kMaxDevices) return AGIS_ERR_ARG;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[device]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_tile_sums);
+        if (e != cudaSuccess || !p) return AGIS_ERR_CUDA;
+        g_noalloc_ptr[device] = (uint64_t *)p;
+    }
+    *out = g_noalloc_ptr[device];
+    return AGIS_OK;
+}
+
+}  // namespace
+}  // namespace agis
+
+extern "C" int agis_prefix_sum_u64_noalloc(const uint64_t *in, int64_t n, uint64_t *out, void *cuda_stream)
+{
+    using namespace agis;
+    if (n < 0 || (n > 0 && (!in || !out))) return AGIS_ERR_ARG;
+    if (n > kNoAllocMaxN) return AGIS_ERR_ARG;
+    if (n == 0) return AGIS_OK;
+    int device = 0;
+    AGIS_CUDA_TRY(cudaGetDevice(&device));
+    uint64_t *tile_sums = nullptr;
+    int rc = noalloc_scratch(device, &tile_sums);
+    if (rc != AGIS_OK) return rc;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const int64_t tiles = (n + kScanTile - 1) / kScanTile;
+    // every tile sum read below is written first by k_scan_tile_sums, so the
+    // array needs no clearing between calls
+    count_launch();
+    k_scan_tile_sums<<<(unsigned)tiles, kScanThreads, 0, st>>>(in, n, tile_sums);
+    count_launch();
+    k_scan_single<<<1, kScanThreads, 0, st>>>(tile_sums, tiles);
+    count_launch();
+    k_scan_apply<<<(unsigned)tiles, kScanThreads, 0, st>>>(in, n, tile_sums, out);
+    return cuda_status(cudaGetLastError());
+}
