@@ -403,6 +403,34 @@ def run_gpu(args, world, rank, local):
         trials_per_step = trials * len(names)
         value = trials_per_step * world / (ms / 1000.0)
 
+        # random 32-byte-sector read bandwidth over 16 GB (the random-access roofline)
+        rand_gbs = None
+        try:
+            buf = torch.empty(16 << 30, dtype=torch.uint8, device="cuda")
+            sink = torch.zeros(1, dtype=torch.int64, device="cuda")
+            sms = torch.cuda.get_device_properties(local).multi_processor_count
+            threads = sms * 2048
+            reads = 1 << 30
+            per = -(-reads // threads)
+            per = -(-per // 8) * 8
+            issued = threads * per
+            best = None
+            for rep in range(4):
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                agis.probe_random_read(buf.data_ptr(), buf.numel(), reads, rep + 1, stream.cuda_stream, sink.data_ptr())
+                b.record(stream)
+                b.synchronize()
+                ms_r = a.elapsed_time(b)
+                if rep > 0 and (best is None or ms_r < best):
+                    best = ms_r
+            rand_gbs = issued * 32 / (best / 1000.0) / 1e9
+            del buf
+            torch.cuda.empty_cache()
+        except Exception:
+            rand_gbs = None
+
         # roofline of the sampler kernel: algorithmic sectors / its own event time
         samp_ms = [sum(t["sample"]) for t, _ in recs]
         sectors = [sum(r[1] for r in res) for _, res in recs]
@@ -511,6 +539,8 @@ def run_gpu(args, world, rank, local):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "kernel": "sample_kernel",
                      "peak_kind": peak_kind, "per_launch_ms": per_launch_ms,
+                     "random_access_gbs": rand_gbs,
+                     "frac_of_random_access": (achieved / rand_gbs) if rand_gbs else None,
                      "algorithmic_bytes_per_launch": statistics.mean(sectors) * 32 / len(names)},
         "cpu_baseline": cpu,
         "e2e": e2e,

@@ -250,6 +250,16 @@ int agis_prepare(agis_graph *g, const agis_pattern *p, const agis_opts *opts);
  * caller.  Errors: ARG (n < 0, n too large, null pointer), CUDA. */
 int agis_prefix_sum_u64_noalloc(const uint64_t *in, int64_t n, uint64_t *out, void *cuda_stream);
 
+/* agis_probe_random_read: enqueues (on cuda_stream) about `reads` independent reads,
+ * each of the first 8 bytes of a random 32-byte sector of the device buffer buf
+ * (bytes long; choose it far larger than L2), as a measure of the random-access
+ * bandwidth that bounds the sampler's gathers and searches (the roofline of
+ * Alg. 3's memory pattern).  The exact count issued is a multiple of
+ * 8 * 2048 * (number of SMs) >= reads; sink is a device uint64 the kernel may
+ * write.  Time it with events on the same stream.  Errors: ARG, CUDA. */
+int agis_probe_random_read(const void *buf, uint64_t bytes, uint64_t reads, uint64_t seed,
+                           void *cuda_stream, void *sink);
+
 /* agis_kernel_launches: number of this library's CUDA kernel launches so far in
  * the process (all contexts); a diagnostic for counting device work. */
 uint64_t agis_kernel_launches(void);

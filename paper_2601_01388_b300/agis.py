@@ -32,7 +32,7 @@ EXPORTS = [
     "agis_graph_row_prefix", "agis_graph_validate", "agis_graph_copy_csr", "agis_graph_drop_tables", "agis_graph_free", "agis_graph_generate_rmat",
     "agis_pattern_create", "agis_pattern_info", "agis_pattern_decide", "agis_pattern_free",
     "agis_estimate", "agis_estimate_batch", "agis_autotune", "agis_dump_trials", "agis_sample_device",
-    "agis_prepare", "agis_z_of_delta", "agis_kernel_launches", "agis_prefix_sum_u64_noalloc", "agis_server_create", "agis_server_submit", "agis_server_poll",
+    "agis_prepare", "agis_z_of_delta", "agis_kernel_launches", "agis_prefix_sum_u64_noalloc", "agis_probe_random_read", "agis_server_create", "agis_server_submit", "agis_server_poll",
     "agis_server_stats", "agis_server_destroy",
 ]
 
@@ -86,6 +86,7 @@ _sig = {
     "agis_z_of_delta": ([C.c_double], C.c_double),
     "agis_kernel_launches": ([], C.c_uint64),
     "agis_prefix_sum_u64_noalloc": ([VP, C.c_int64, VP, VP], C.c_int),
+    "agis_probe_random_read": ([VP, C.c_uint64, C.c_uint64, C.c_uint64, VP, VP], C.c_int),
     "agis_server_create": ([VP, C.c_size_t, C.c_int, P(VP)], C.c_int),
     "agis_server_submit": ([VP, VP, P(Opts), P(C.c_uint64)], C.c_int),
     "agis_server_poll": ([VP, C.c_uint64, P(Result), P(C.c_double)], C.c_int),
@@ -133,6 +134,14 @@ def prefix_sum_u64_noalloc(in_ptr: int, n: int, out_ptr: int, stream: int = 0):
     _check(_lib.agis_prefix_sum_u64_noalloc(C.c_void_p(in_ptr), n, C.c_void_p(out_ptr),
                                             C.c_void_p(stream) if stream else None),
            "agis_prefix_sum_u64_noalloc")
+
+
+def probe_random_read(buf_ptr: int, nbytes: int, reads: int, seed: int, stream: int, sink_ptr: int) -> int:
+    """Enqueues the random 32-byte-sector read probe; returns the reads issued."""
+    _check(_lib.agis_probe_random_read(C.c_void_p(buf_ptr), nbytes, reads, seed,
+                                       C.c_void_p(stream) if stream else None, C.c_void_p(sink_ptr)),
+           "agis_probe_random_read")
+    return reads
 
 
 def kernel_launches():

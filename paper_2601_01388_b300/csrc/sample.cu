@@ -173,7 +173,8 @@ struct WarpSets {
 
 // Keeps the entries of the ascending list L[0, n) that are not trajectory members
 // (tau_s[0, tau_n)) and that occur in the ascending row R[0, m) (all of them when R
-// is null); survivors are appended, in order, to out.  With kWeigh the survivors'
+// is null); survivors are appended, in order, to out (room for cap; a return value
+// above cap means the list overflowed and out is incomplete).  With kWeigh the survivors'
 // weights (q[x] under f_approx, 1 under f_uniform) are accumulated into out_pw as
 // inclusive running sums and *W receives the total.
 //
@@ -186,14 +187,15 @@ struct WarpSets {
 // weights when kWeigh; cnt and carry advance.
 template <bool kWeigh>
 __device__ __forceinline__ void emit_window(bool ok, int32_t x, uint64_t w, int32_t *out, uint64_t *out_pw,
-                                            uint32_t &cnt, uint64_t &carry, int lane)
+                                            uint32_t cap, uint32_t &cnt, uint64_t &carry, int lane)
 {
     const uint32_t bal = __ballot_sync(kFull, ok);
     const uint32_t pos = cnt + __popc(bal & ((1u << lane) - 1u));
-    if (ok) out[pos] = x;
+    const bool store = ok && pos < cap;
+    if (store) out[pos] = x;
     if (kWeigh) {
         const uint64_t incl = warp_incl_scan(ok ? w : 0u, lane);
-        if (ok) out_pw[pos] = carry + incl;
+        if (store) out_pw[pos] = carry + incl;
         carry += __shfl_sync(kFull, incl, 31);
     }
     cnt += __popc(bal);
@@ -201,7 +203,8 @@ __device__ __forceinline__ void emit_window(bool ok, int32_t x, uint64_t w, int3
 
 // Keeps the entries of the ascending list L[0, n) that are not trajectory members
 // (tau_s[0, tau_n)) and that occur in the ascending row R[0, m) (all of them when R
-// is null); survivors are appended, in order, to out.  With kWeigh the survivors'
+// is null); survivors are appended, in order, to out (room for cap; a return value
+// above cap means the list overflowed and out is incomplete).  With kWeigh the survivors'
 // weights (q[x] under f_approx, 1 under f_uniform) are accumulated into out_pw as
 // inclusive running sums and *W receives the total.
 //
@@ -214,7 +217,8 @@ __device__ __forceinline__ void emit_window(bool ok, int32_t x, uint64_t w, int3
 template <bool kWeigh>
 __device__ uint32_t filter_list(const int32_t *L, uint32_t n, const int32_t *R, int64_t m,
                                 const uint32_t *Rbits, const int32_t *tau_s, int tau_n, int32_t *out,
-                                uint64_t *out_pw, const uint64_t *q, bool approx, uint64_t *W, int lane)
+                                uint64_t *out_pw, uint32_t cap, const uint64_t *q, bool approx, uint64_t *W,
+                                int lane)
 {
     uint32_t cnt = 0;
     uint64_t carry = 0;
@@ -238,7 +242,8 @@ __device__ uint32_t filter_list(const int32_t *L, uint32_t n, const int32_t *R, 
 #pragma unroll
             for (int u = 0; u < U; ++u) w[u] = (kWeigh && ok[u]) ? (approx ? __ldg(q + x[u]) : 1u) : 0u;
 #pragma unroll
-            for (int u = 0; u < U; ++u) emit_window<kWeigh>(ok[u], x[u], w[u], out, out_pw, cnt, carry, lane);
+            for (int u = 0; u < U; ++u) emit_window<kWeigh>(ok[u], x[u], w[u], out, out_pw, cap, cnt, carry, lane);
+            if (cnt > cap) return cnt;         // list full: the caller takes the list-free path
         }
         if (kWeigh) *W = carry;
         return cnt;
@@ -281,7 +286,8 @@ __device__ uint32_t filter_list(const int32_t *L, uint32_t n, const int32_t *R, 
             ok = row_find(R, m, x) >= 0;
         }
         const uint64_t w = (kWeigh && ok) ? (approx ? __ldg(q + x) : 1u) : 0u;
-        emit_window<kWeigh>(ok, x, w, out, out_pw, cnt, carry, lane);
+        emit_window<kWeigh>(ok, x, w, out, out_pw, cap, cnt, carry, lane);
+        if (cnt > cap) return cnt;
     }
     if (kWeigh) *W = carry;
     return cnt;
@@ -372,13 +378,14 @@ __device__ TrialOut run_trial(const GraphView &g, const DevQuery &Q, uint64_t t,
             // S of the previous step is reusable when this step's backward set is the
             // previous one plus the previous vertex: S_i = S_{i-1} & N(v_{i-1})
             const bool reuse = S.inc && cur >= 0;
-            const uint32_t n_src = reuse ? n_cur : (uint32_t)(da < (int64_t)ws.cap ? da : ws.cap);
-            if (ws.cap > 0 && (reuse || da <= (int64_t)ws.cap)) {
+            const uint32_t n_src = reuse ? n_cur : (uint32_t)da;
+            bool listed = false;
+            int nxt = reuse ? 1 - cur : 0;
+            uint32_t n = n_src;
+            uint64_t Wl = 0;
+            if (ws.cap > 0 && (reuse || da < 0x7fffffffll)) {
                 const int32_t *src = reuse ? ws.xs[cur] : g.cols + a_start;
                 const int tau_n = reuse ? 0 : i;
-                int nxt = reuse ? 1 - cur : 0;
-                uint32_t n = n_src;
-                uint64_t Wl = 0;
                 const int passes = reuse ? 1 : (n_other > 0 ? n_other : 1);
                 for (int pss = 0; pss < passes; ++pss) {
                     const int32_t *R = nullptr;
@@ -396,15 +403,19 @@ __device__ TrialOut run_trial(const GraphView &g, const DevQuery &Q, uint64_t t,
                     }
                     if (pss == passes - 1) {
                         n = filter_list<true>(src, n, R, m, Rb, tau_s, pss == 0 ? tau_n : 0, ws.xs[nxt],
-                                              ws.pw[nxt], S.q, S.approx != 0, &Wl, lane);
+                                              ws.pw[nxt], ws.cap, S.q, S.approx != 0, &Wl, lane);
                     } else {
                         n = filter_list<false>(src, n, R, m, Rb, tau_s, pss == 0 ? tau_n : 0, ws.xs[nxt],
-                                               nullptr, S.q, S.approx != 0, nullptr, lane);
+                                               nullptr, ws.cap, S.q, S.approx != 0, nullptr, lane);
                         src = ws.xs[nxt];
                         nxt = 1 - nxt;
                     }
+                    if (n > ws.cap) break;
                 }
                 __syncwarp();
+                listed = n <= ws.cap;
+            }
+            if (listed) {
                 if (S.approx && S.nb > 1) sec += n;
                 W = Wl;
                 cur = nxt;
