@@ -251,8 +251,8 @@ int agis_prepare(agis_graph *g, const agis_pattern *p, const agis_opts *opts);
 int agis_prefix_sum_u64_noalloc(const uint64_t *in, int64_t n, uint64_t *out, void *cuda_stream);
 
 /* agis_probe_random_read: enqueues (on cuda_stream) about `reads` independent reads,
- * each of the first 8 bytes of a random 32-byte sector of the device buffer buf
- * (bytes long; choose it far larger than L2), as a measure of the random-access
+ * each of the first 8 bytes of a random 32-byte sector among the first 2^k sectors
+ * of the device buffer buf (bytes long, 2^k*32 <= bytes; choose it far larger than L2), as a measure of the random-access
  * bandwidth that bounds the sampler's gathers and searches (the roofline of
  * Alg. 3's memory pattern).  The exact count issued is a multiple of
  * 8 * 2048 * (number of SMs) >= reads; sink is a device uint64 the kernel may

@@ -16,8 +16,9 @@ __device__ __forceinline__ uint64_t mix64(uint64_t x)
 }
 
 // Every thread reads `per_thread` 8-byte words, each at the start of a random
-// 32-byte sector; the xor of the words goes to sink so the loads stay.
-__global__ void k_random_read(const uint64_t *buf, uint64_t sectors, uint64_t per_thread, uint64_t seed,
+// 32-byte sector among the first sector_mask + 1 (a power of two); the xor of the
+// words goes to sink so the loads stay.
+__global__ void k_random_read(const uint64_t *buf, uint64_t sector_mask, uint64_t per_thread, uint64_t seed,
                               unsigned long long *sink)
 {
     const uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
@@ -29,7 +30,7 @@ __global__ void k_random_read(const uint64_t *buf, uint64_t sectors, uint64_t pe
 #pragma unroll
         for (int j = 0; j < kInFlight; ++j) {
             h = mix64(h);
-            v[j] = __ldcg(buf + (h % sectors) * 4);
+            v[j] = __ldcg(buf + (h & sector_mask) * 4);
         }
 #pragma unroll
         for (int j = 0; j < kInFlight; ++j) acc ^= v[j];
@@ -51,8 +52,10 @@ extern "C" int agis_probe_random_read(const void *buf, uint64_t bytes, uint64_t 
     const uint64_t threads = (uint64_t)sms * 2048;
     uint64_t per = (reads + threads - 1) / threads;
     per = (per + 7) / 8 * 8;
+    uint64_t sectors = 1;
+    while (sectors * 2 <= bytes / 32) sectors *= 2;
     count_launch();
     k_random_read<<<(unsigned)(threads / 256), 256, 0, (cudaStream_t)cuda_stream>>>(
-        (const uint64_t *)buf, bytes / 32, per, seed, (unsigned long long *)sink);
+        (const uint64_t *)buf, sectors - 1, per, seed, (unsigned long long *)sink);
     return cuda_status(cudaGetLastError());
 }

@@ -90,19 +90,26 @@ __device__ __forceinline__ uint64_t excluded_upto(int64_t pos, uint32_t xmask, i
     return s;
 }
 
-// First index j in [0, n) with F(j) > r, where F(j) = P[j] - (excluded weight at
-// positions <= j), or F(j) = j + 1 - (excluded count ...) when P is null.  F is
-// non-decreasing and F(n-1) > r.  Each round splits the range into 32 parts and
-// one ballot picks the part, so a row of d entries takes ceil(log32 d) rounds.
-__device__ int64_t warp_find(const uint64_t *P, int64_t n, uint64_t r, uint32_t xmask, int64_t xp,
-                             uint64_t xq, int lane)
+// First index j in [0, n) with F(j) > r, where F(j) = P[j] minus the excluded
+// weight at or before j (or F(j) = j + 1 minus the excluded count when P is null).
+// Excluded entries live one per lane (bits of xmask) as a key and a weight; the key
+// is a position, or, when ids (the row's ascending vertex ids) is given, a vertex
+// id compared with ids[j].  F is non-decreasing and F(n-1) > r.  Each round splits
+// the range into 32 parts and one ballot picks the part, so a row of d entries takes
+// ceil(log32 d) rounds of independent loads.
+__device__ int64_t warp_find(const uint64_t *P, int64_t n, uint64_t r, uint32_t xmask, int64_t xkey,
+                             uint64_t xq, const int32_t *ids, int lane)
 {
     int64_t lo = 0, hi = n;
     while (hi - lo > 32) {
         const int64_t step = (hi - lo + 31) >> 5;
         const int64_t pos = lo + (int64_t)(lane + 1) * step - 1;
         const int64_t cpos = pos < hi - 1 ? pos : hi - 1;
-        const uint64_t ex = excluded_upto(cpos, xmask, xp, xq);
+        uint64_t ex = 0;
+        if (xmask) {
+            const int64_t key = ids ? (int64_t)__ldg(ids + cpos) : cpos;
+            ex = excluded_upto(key, xmask, xkey, xq);
+        }
         bool gt = true;
         if (pos < hi - 1) {
             const uint64_t f = (P ? __ldg(P + pos) : (uint64_t)(pos + 1)) - ex;
@@ -116,10 +123,59 @@ __device__ int64_t warp_find(const uint64_t *P, int64_t n, uint64_t r, uint32_t 
     }
     const int64_t pos = lo + lane;
     const int64_t cpos = pos < hi ? pos : hi - 1;
-    const uint64_t ex = excluded_upto(cpos, xmask, xp, xq);
+    uint64_t ex = 0;
+    if (xmask) {
+        const int64_t key = ids ? (int64_t)__ldg(ids + cpos) : cpos;
+        ex = excluded_upto(key, xmask, xkey, xq);
+    }
     bool gt = true;
     if (pos < hi) gt = ((P ? __ldg(P + pos) : (uint64_t)(pos + 1)) - ex) > r;
     return lo + (__ffs(__ballot_sync(kFull, gt)) - 1);
+}
+
+// The first two rounds of warp_find over the step-1 prefix (n = nv) always read
+// the same 32 + 32*32 splitters; they are staged in shared memory per query.
+constexpr int kTopSplitters = 32 + 32 * 32;
+
+__device__ __forceinline__ int64_t top_step(int64_t lo, int64_t hi) { return (hi - lo + 31) >> 5; }
+
+// Position of splitter k of the two cached levels (level 1: k < 32; level 2: part
+// f = (k-32)/32, lane (k-32)%32), or -1 where the search never reads one.
+__device__ __forceinline__ int64_t top_pos(int64_t n, int k)
+{
+    if (n <= 32) return -1;
+    const int64_t s1 = top_step(0, n);
+    if (k < 32) {
+        const int64_t pos = (int64_t)(k + 1) * s1 - 1;
+        return pos < n - 1 ? pos : -1;
+    }
+    const int f = (k - 32) >> 5, l = (k - 32) & 31;
+    const int64_t lo = (int64_t)f * s1, hi = lo + s1 < n ? lo + s1 : n;
+    if (lo >= n || hi - lo <= 32) return -1;
+    const int64_t pos = lo + (int64_t)(l + 1) * top_step(lo, hi) - 1;
+    return pos < hi - 1 ? pos : -1;
+}
+
+// warp_find over P[0, n) (no exclusions) whose first two rounds use the staged
+// splitters top[k] = P[top_pos(n, k)].
+__device__ int64_t warp_find_top(const uint64_t *P, int64_t n, uint64_t r, const uint64_t *top, int lane)
+{
+    int64_t lo = 0, hi = n;
+    for (int level = 0; level < 2 && hi - lo > 32; ++level) {
+        const int64_t step = (hi - lo + 31) >> 5;
+        const int64_t pos = lo + (int64_t)(lane + 1) * step - 1;
+        bool gt = true;
+        if (pos < hi - 1) {
+            const int k = level == 0 ? lane : 32 + (int)(lo / top_step(0, n)) * 32 + lane;
+            gt = top[k] > r;
+        }
+        const int f = __ffs(__ballot_sync(kFull, gt)) - 1;
+        const int64_t nlo = lo + (int64_t)f * step;
+        const int64_t nhi = lo + (int64_t)(f + 1) * step;
+        lo = nlo;
+        hi = nhi < hi ? nhi : hi;
+    }
+    return lo + warp_find(P + lo, hi - lo, r, 0u, 0, 0, nullptr, lane);
 }
 
 __device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v)
@@ -296,7 +352,7 @@ __device__ uint32_t filter_list(const int32_t *L, uint32_t n, const int32_t *R, 
 // Alg. 3 for trial t of query Q; all 32 lanes call it together.  tau_s is the
 // warp's shared-memory copy of the trajectory.
 __device__ TrialOut run_trial(const GraphView &g, const DevQuery &Q, uint64_t t, int32_t *tau_s,
-                              const WarpSets &ws, int lane)
+                              const WarpSets &ws, const uint64_t *top, int lane)
 {
     TrialOut out{0.0, 0, 0};
     double X = 1.0;
@@ -316,7 +372,7 @@ __device__ TrialOut run_trial(const GraphView &g, const DevQuery &Q, uint64_t t,
             if (W == 0) { out.sectors = sec; return out; }
             const uint64_t r = draw_below(W, t, 1, kStreamTrial, Q.seed);
             const uint64_t *P = S.approx ? S.pref : (const uint64_t *)(g.off + 1);
-            v = (int32_t)warp_find(P, g.nv, r, 0u, 0, 0, lane);
+            v = (int32_t)warp_find_top(P, g.nv, r, top, lane);
             qv = S.approx ? __ldg(S.q + v) : (uint64_t)(__ldg(g.off + v + 1) - __ldg(g.off + v));
             cur = -1;
         } else if (S.nb == 1 && (S.pref != nullptr || !S.approx)) {
@@ -326,23 +382,28 @@ __device__ TrialOut run_trial(const GraphView &g, const DevQuery &Q, uint64_t t,
             const int64_t a_start = __ldg(g.off + a);
             const int64_t d = __ldg(g.off + a + 1) - a_start;
             sec += 1 + (uint64_t)(i - 1) * sec_search(d, 4) + (S.approx ? sec_search(d, 8) + 1 : 0) + 1;
-            // trajectory members inside a's row (lane j checks tau_j)
-            int64_t xp = -1;
+            // trajectory members inside a's row (lane j checks tau_j): excluded by
+            // vertex id, so a hub row needs one bitmap probe and no search
+            bool member = false;
+            int64_t xkey = -1;
             uint64_t xq = 0;
             const uint32_t *abits = bits_of(g, a);
             if (lane < i && lane != jb) {
                 const int32_t m = tau_s[lane];
-                if (!abits || bit_test(abits, m)) xp = row_find(g.cols + a_start, d, m);
-                if (xp >= 0) xq = S.approx ? __ldg(S.q + m) : 1u;
+                member = abits ? bit_test(abits, m) : row_find(g.cols + a_start, d, m) >= 0;
+                if (member) {
+                    xkey = m;
+                    xq = S.approx ? __ldg(S.q + m) : 1u;
+                }
             }
-            const uint32_t xmask = __ballot_sync(kFull, xp >= 0);
+            const uint32_t xmask = __ballot_sync(kFull, member);
             const uint64_t excl = warp_sum_u64(xq);
             const uint64_t *P = S.approx ? S.pref + a_start : nullptr;
             const uint64_t total = d <= 0 ? 0 : (S.approx ? __ldg(P + d - 1) : (uint64_t)d);
             W = total - excl;
             if (W == 0) { out.sectors = sec; return out; }
             const uint64_t r = draw_below(W, t, (uint64_t)(i + 1), kStreamTrial, Q.seed);
-            const int64_t pos = warp_find(P, d, r, xmask, xp, xq, lane);
+            const int64_t pos = warp_find(P, d, r, xmask, xkey, xq, g.cols + a_start, lane);
             v = __ldg(g.cols + a_start + pos);
             qv = S.approx ? __ldg(S.q + v) : 1u;
             cur = -1;
@@ -422,7 +483,7 @@ __device__ TrialOut run_trial(const GraphView &g, const DevQuery &Q, uint64_t t,
                 n_cur = n;
                 if (W == 0) { out.sectors = sec; return out; }
                 const uint64_t r = draw_below(W, t, (uint64_t)(i + 1), kStreamTrial, Q.seed);
-                const int64_t j = warp_find(ws.pw[cur], n, r, 0u, 0, 0, lane);
+                const int64_t j = warp_find(ws.pw[cur], n, r, 0u, 0, 0, nullptr, lane);
                 v = ws.xs[cur][j];
                 qv = ws.pw[cur][j] - (j > 0 ? ws.pw[cur][j - 1] : 0);
                 X = X * ((double)W / (double)qv);
@@ -512,7 +573,7 @@ __device__ TrialOut run_trial(const GraphView &g, const DevQuery &Q, uint64_t t,
 // trials [implicit_first + 1024 j, ...) of query 0 up to implicit_count trials and
 // writes slot j.  n_items_ptr[0] holds the number of items.
 template <bool kDump>
-__global__ void __launch_bounds__(kBlock, 3) sample_kernel(GraphView g, const DevQuery *__restrict__ queries,
+__global__ void __launch_bounds__(kBlock, 4) sample_kernel(GraphView g, const DevQuery *__restrict__ queries,
                                                         const WorkItem *__restrict__ items,
                                                         const uint32_t *__restrict__ n_items_ptr,
                                                         uint32_t *counter, uint64_t *tile_out,
@@ -525,6 +586,7 @@ __global__ void __launch_bounds__(kBlock, 3) sample_kernel(GraphView g, const De
     __shared__ double red[kBlock];
     __shared__ double red2[kBlock];
     __shared__ int32_t tau_s[kWarps][kMaxK];
+    __shared__ uint64_t s_top[kTopSplitters];
     __shared__ uint32_t s_item, s_next, s_hits;
     __shared__ unsigned long long s_sec;
     __shared__ int s_query, s_reload;
@@ -576,6 +638,12 @@ __global__ void __launch_bounds__(kBlock, 3) sample_kernel(GraphView g, const De
             const uint32_t *src = (const uint32_t *)(queries + it.query);
             uint32_t *dst = (uint32_t *)&sq;
             for (int j = threadIdx.x; j < words; j += kBlock) dst[j] = src[j];
+            __syncthreads();
+            const uint64_t *P = sq.step[0].approx ? sq.step[0].pref : (const uint64_t *)(g.off + 1);
+            for (int k = threadIdx.x; k < kTopSplitters; k += kBlock) {
+                const int64_t pos = top_pos(g.nv, k);
+                s_top[k] = pos >= 0 ? __ldg(P + pos) : 0;
+            }
         }
         for (int j = threadIdx.x; j < kTile; j += kBlock) xs[j] = 0.0;
         __syncthreads();
@@ -585,7 +653,7 @@ __global__ void __launch_bounds__(kBlock, 3) sample_kernel(GraphView g, const De
             tt = __shfl_sync(kFull, tt, 0);
             if (tt >= it.count) break;
             const uint64_t t = it.first + tt;
-            const TrialOut r = run_trial(g, sq, t, tau_s[warp], ws, lane);
+            const TrialOut r = run_trial(g, sq, t, tau_s[warp], ws, s_top, lane);
             if (lane == 0) {
                 xs[tt] = r.x;
                 if (r.hit) atomicAdd(&s_hits, 1u);
