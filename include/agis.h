@@ -163,6 +163,15 @@ int agis_graph_free(agis_graph *g);
 int agis_graph_generate_rmat(agis_ctx *ctx, int scale, int edge_factor, double a, double b,
                              double c, uint64_t seed, agis_graph **out);
 
+/* agis_graph_generate_chunglu: Chung-Lu graph (Chung & Lu, PNAS 2002) on n
+ * vertices with expected degrees proportional to (i + i0)^(-1/(gamma-1)), scaled
+ * to mean_degree (i0 keeps the largest below sqrt(n * mean_degree)); n*mean/2
+ * edge draws with both endpoints drawn in proportion to the weights, symmetrised,
+ * loops and duplicates removed, ids permuted by a seeded bijection; built on the
+ * device.  Errors: ARG, NOMEM, CUDA. */
+int agis_graph_generate_chunglu(agis_ctx *ctx, int64_t n, double gamma, double mean_degree,
+                                uint64_t seed, agis_graph **out);
+
 /* ---- pattern -------------------------------------------------------------
  * agis_pattern_create: k vertices (2..8), ne undirected edges as pairs
  * edge_pairs[2*ne] (host).  Computes the matching order pi (Alg. 2, ties to the
@@ -259,6 +268,14 @@ int agis_prefix_sum_u64_noalloc(const uint64_t *in, int64_t n, uint64_t *out, vo
  * write.  Time it with events on the same stream.  Errors: ARG, CUDA. */
 int agis_probe_random_read(const void *buf, uint64_t bytes, uint64_t reads, uint64_t seed,
                            void *cuda_stream, void *sink);
+
+/* agis_step_timers: reads (and with reset != 0 clears) the sampler's per-step-kind
+ * cycle counters of the current device: out16[2k] = summed SM cycles, out16[2k+1]
+ * = number of steps, for kinds k = 0 step 1, 1 single-backward search, 2 listed
+ * intersection, 3 listed reuse of the previous list, 4 list-free scan.  They are
+ * only counted in a build with -DAGIS_STEP_TIMERS (zeros otherwise).  A profiling
+ * aid.  Errors: ARG, CUDA. */
+int agis_step_timers(uint64_t *out16, int reset);
 
 /* agis_kernel_launches: number of this library's CUDA kernel launches so far in
  * the process (all contexts); a diagnostic for counting device work. */

@@ -29,10 +29,10 @@ TILE = 1024
 EXPORTS = [
     "agis_status_str", "agis_default_opts", "agis_create", "agis_destroy", "agis_graph_load_csr",
     "agis_graph_preprocess", "agis_graph_info", "agis_graph_stats_copy", "agis_graph_weight_table",
-    "agis_graph_row_prefix", "agis_graph_validate", "agis_graph_copy_csr", "agis_graph_drop_tables", "agis_graph_free", "agis_graph_generate_rmat",
+    "agis_graph_row_prefix", "agis_graph_validate", "agis_graph_copy_csr", "agis_graph_drop_tables", "agis_graph_free", "agis_graph_generate_rmat", "agis_graph_generate_chunglu",
     "agis_pattern_create", "agis_pattern_info", "agis_pattern_decide", "agis_pattern_free",
     "agis_estimate", "agis_estimate_batch", "agis_autotune", "agis_dump_trials", "agis_sample_device",
-    "agis_prepare", "agis_z_of_delta", "agis_kernel_launches", "agis_prefix_sum_u64_noalloc", "agis_probe_random_read", "agis_server_create", "agis_server_submit", "agis_server_poll",
+    "agis_prepare", "agis_z_of_delta", "agis_kernel_launches", "agis_prefix_sum_u64_noalloc", "agis_probe_random_read", "agis_step_timers", "agis_server_create", "agis_server_submit", "agis_server_poll",
     "agis_server_stats", "agis_server_destroy",
 ]
 
@@ -73,6 +73,7 @@ _sig = {
     "agis_graph_drop_tables": ([VP], C.c_int),
     "agis_graph_free": ([VP], C.c_int),
     "agis_graph_generate_rmat": ([VP, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, C.c_uint64, P(VP)], C.c_int),
+    "agis_graph_generate_chunglu": ([VP, C.c_int64, C.c_double, C.c_double, C.c_uint64, P(VP)], C.c_int),
     "agis_pattern_create": ([C.c_int, C.c_int, P(C.c_int32), P(VP)], C.c_int),
     "agis_pattern_info": ([VP, P(C.c_int32), P(C.c_int32), P(C.c_int32), P(C.c_double), P(C.c_uint8), P(C.c_uint64)], C.c_int),
     "agis_pattern_decide": ([VP, C.c_int32, C.c_double, P(C.c_uint8)], C.c_int),
@@ -87,6 +88,7 @@ _sig = {
     "agis_kernel_launches": ([], C.c_uint64),
     "agis_prefix_sum_u64_noalloc": ([VP, C.c_int64, VP, VP], C.c_int),
     "agis_probe_random_read": ([VP, C.c_uint64, C.c_uint64, C.c_uint64, VP, VP], C.c_int),
+    "agis_step_timers": ([VP, C.c_int], C.c_int),
     "agis_server_create": ([VP, C.c_size_t, C.c_int, P(VP)], C.c_int),
     "agis_server_submit": ([VP, VP, P(Opts), P(C.c_uint64)], C.c_int),
     "agis_server_poll": ([VP, C.c_uint64, P(Result), P(C.c_double)], C.c_int),
@@ -142,6 +144,14 @@ def probe_random_read(buf_ptr: int, nbytes: int, reads: int, seed: int, stream: 
                                        C.c_void_p(stream) if stream else None, C.c_void_p(sink_ptr)),
            "agis_probe_random_read")
     return reads
+
+
+def step_timers(reset=False):
+    """Per-step-kind (cycles, steps) of the sampler (a -DAGIS_STEP_TIMERS build)."""
+    out = np.zeros(16, dtype=np.uint64)
+    _check(_lib.agis_step_timers(_ptr(out), int(reset)), "agis_step_timers")
+    kinds = ["step1", "single_backward", "listed_intersection", "listed_reuse", "list_free_scan"]
+    return {k: (int(out[2 * i]), int(out[2 * i + 1])) for i, k in enumerate(kinds)}
 
 
 def kernel_launches():
@@ -247,6 +257,16 @@ class Graph:
         h = VP()
         _check(_lib.agis_graph_generate_rmat(ctx.h, scale, edge_factor, a, b, c, seed, C.byref(h)),
                "agis_graph_generate_rmat")
+        self.h = h
+        return self
+
+    @classmethod
+    def chung_lu(cls, ctx, n, gamma=2.1, mean_degree=32.0, seed=1):
+        self = cls.__new__(cls)
+        self.ctx = ctx
+        h = VP()
+        _check(_lib.agis_graph_generate_chunglu(ctx.h, n, gamma, mean_degree, seed, C.byref(h)),
+               "agis_graph_generate_chunglu")
         self.h = h
         return self
 

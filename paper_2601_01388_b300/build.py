@@ -25,6 +25,8 @@ def headers():
 def needs_build() -> bool:
     if not os.path.exists(LIB):
         return True
+    if os.environ.get("AGIS_NVCC_FLAGS"):
+        return True
     t = os.path.getmtime(LIB)
     return any(os.path.getmtime(f) > t for f in sources() + headers())
 
@@ -36,6 +38,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     cmd = [nvcc, "-O3", "-std=c++17", *ARCH, "-lineinfo", "-fmad=false", "-Xcompiler", "-fPIC",
            "-Xcompiler", "-O2", "-shared", "-I", os.path.join(ROOT, "include"),
            "-o", LIB + ".tmp", *sources(), "-lcudart"]
+    extra = os.environ.get("AGIS_NVCC_FLAGS", "").split()
+    cmd[1:1] = extra
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     r = subprocess.run(cmd, capture_output=True, text=True)

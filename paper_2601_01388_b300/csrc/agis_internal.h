@@ -161,6 +161,7 @@ namespace agis {
 
 // graph.cu
 int build_hub_bitmaps(agis_graph *g);
+int inclusive_scan_u64(agis_ctx *ctx, const uint64_t *in, int64_t n, uint64_t *out);
 int build_weight_table(agis_graph *g, const int32_t cfg[4], bool need_pref, bool need_rowp,
                        WeightTable **out);
 uint64_t cfg_key(const int32_t cfg[4]);

@@ -295,7 +295,14 @@ int grid_stride_blocks(const agis_graph *g, int64_t work, int threads)
 
 int inclusive_scan(agis_graph *g, const uint64_t *in, int64_t n, uint64_t *out)
 {
-    cudaStream_t st = g->ctx->stream;
+    return inclusive_scan_u64(g->ctx, in, n, out);
+}
+
+}  // namespace
+
+int inclusive_scan_u64(agis_ctx *ctx, const uint64_t *in, int64_t n, uint64_t *out)
+{
+    cudaStream_t st = ctx->stream;
     const int64_t tiles = (n + kScanTile - 1) / kScanTile;
     if (tiles == 0) return AGIS_OK;
     uint64_t *tile_sums = nullptr;
@@ -311,7 +318,6 @@ int inclusive_scan(agis_graph *g, const uint64_t *in, int64_t n, uint64_t *out)
     return cuda_status(e);
 }
 
-}  // namespace
 
 // Bitmaps for every vertex of degree >= max(1024, t), t the smallest degree whose
 // hub set fits a sixteenth of device memory (nv bits per hub).  A membership test

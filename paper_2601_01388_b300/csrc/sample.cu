@@ -22,10 +22,30 @@
 #include "agis_internal.h"
 #include "philox.cuh"
 
+// Resident CTAs per SM the register allocation is sized for (the build may
+// override it; the autotuner then picks up to this many).
+#ifndef AGIS_MIN_BLOCKS
+#define AGIS_MIN_BLOCKS 4
+#endif
+
 namespace agis {
+
+// Optional per-step-kind cycle counters (build with -DAGIS_STEP_TIMERS): kinds are
+// 0 step 1, 1 single-backward search, 2 listed intersection, 3 listed reuse,
+// 4 list-free scan; entry 2k is cycles, 2k+1 the number of steps.
+__device__ unsigned long long g_step_timers[16];
+
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
+
+#ifdef AGIS_STEP_TIMERS
+#define STEP_T0 long long _t0 = clock64();
+#define STEP_T1(kind) if (lane == 0) { atomicAdd(&g_step_timers[2 * (kind)], (unsigned long long)(clock64() - _t0)); atomicAdd(&g_step_timers[2 * (kind) + 1], 1ull); }
+#else
+#define STEP_T0
+#define STEP_T1(kind)
+#endif
 
 // ---------------------------------------------------------------- cost model
 // Sectors of a search over L entries of w bytes: ceil(log2(ceil(L*w/32))) + 1.
@@ -365,6 +385,7 @@ __device__ TrialOut run_trial(const GraphView &g, const DevQuery &Q, uint64_t t,
         const DevStep &S = Q.step[i];
         uint64_t W = 0, qv = 0;
         int32_t v = -1;
+        STEP_T0
         if (i == 0) {
             // ---- step 1: the whole vertex set
             W = Q.W1;
@@ -375,6 +396,7 @@ __device__ TrialOut run_trial(const GraphView &g, const DevQuery &Q, uint64_t t,
             v = (int32_t)warp_find_top(P, g.nv, r, top, lane);
             qv = S.approx ? __ldg(S.q + v) : (uint64_t)(__ldg(g.off + v + 1) - __ldg(g.off + v));
             cur = -1;
+            STEP_T1(0)
         } else if (S.nb == 1 && (S.pref != nullptr || !S.approx)) {
             // ---- one backward neighbour: S = N(a) \ tau
             const int jb = S.back[0];
@@ -407,6 +429,7 @@ __device__ TrialOut run_trial(const GraphView &g, const DevQuery &Q, uint64_t t,
             v = __ldg(g.cols + a_start + pos);
             qv = S.approx ? __ldg(S.q + v) : 1u;
             cur = -1;
+            STEP_T1(1)
         } else {
             // ---- several backward neighbours (or one, with no row-prefix table):
             //      intersect, anchored at the shortest row
@@ -487,6 +510,7 @@ __device__ TrialOut run_trial(const GraphView &g, const DevQuery &Q, uint64_t t,
                 v = ws.xs[cur][j];
                 qv = ws.pw[cur][j] - (j > 0 ? ws.pw[cur][j - 1] : 0);
                 X = X * ((double)W / (double)qv);
+                STEP_T1(reuse ? 3 : 2)
                 __syncwarp();
                 if (lane == 0) tau_s[i] = v;
                 __syncwarp();
@@ -558,6 +582,7 @@ __device__ TrialOut run_trial(const GraphView &g, const DevQuery &Q, uint64_t t,
                 }
             }
         }
+        if (i > 0 && !(S.nb == 1 && (S.pref != nullptr || !S.approx))) { STEP_T1(4) }
         X = X * ((double)W / (double)qv);
         __syncwarp();
         if (lane == 0) tau_s[i] = v;
@@ -573,7 +598,7 @@ __device__ TrialOut run_trial(const GraphView &g, const DevQuery &Q, uint64_t t,
 // trials [implicit_first + 1024 j, ...) of query 0 up to implicit_count trials and
 // writes slot j.  n_items_ptr[0] holds the number of items.
 template <bool kDump>
-__global__ void __launch_bounds__(kBlock, 4) sample_kernel(GraphView g, const DevQuery *__restrict__ queries,
+__global__ void __launch_bounds__(kBlock, AGIS_MIN_BLOCKS) sample_kernel(GraphView g, const DevQuery *__restrict__ queries,
                                                         const WorkItem *__restrict__ items,
                                                         const uint32_t *__restrict__ n_items_ptr,
                                                         uint32_t *counter, uint64_t *tile_out,
@@ -767,3 +792,14 @@ int add_sampler_node(agis_graph *g, LaunchBuffers &lb, int grid, cudaGraph_t gra
 }
 
 }  // namespace agis
+
+extern "C" int agis_step_timers(uint64_t *out16, int reset)
+{
+    if (!out16) return AGIS_ERR_ARG;
+    AGIS_CUDA_TRY(cudaMemcpyFromSymbol(out16, agis::g_step_timers, 16 * sizeof(uint64_t)));
+    if (reset) {
+        static const uint64_t zero[16] = {0};
+        AGIS_CUDA_TRY(cudaMemcpyToSymbol(agis::g_step_timers, zero, sizeof(zero)));
+    }
+    return AGIS_OK;
+}

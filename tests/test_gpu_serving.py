@@ -145,3 +145,21 @@ def test_device_rmat_is_a_valid_graph(agis):
     g.preprocess(1, CMIN)
     r = agis.estimate(g, agis.Pattern(*I.PATTERNS["triangle"]), agis.default_opts(eps=0.0, max_trials=1 << 16))
     assert r["hits"] > 0
+
+
+def test_device_chung_lu_is_a_valid_power_law_graph(agis):
+    ctx = agis.Context(0)
+    n = 200000
+    g = agis.Graph.chung_lu(ctx, n, 2.1, 32.0, seed=3)
+    g.validate()
+    info = g.info()
+    off, cols = g.csr()
+    deg = np.diff(off)
+    assert info["nv"] == n and len(cols) == info["nnz"]
+    mean = deg.mean()
+    assert 20.0 < mean < 34.0                      # duplicates and loops removed from n*32/2 draws
+    assert deg.max() > 20 * mean                   # heavy tail
+    assert deg.max() <= 2.0 * np.sqrt(32.0 * n)   # capped near sqrt(sum of expected degrees)
+    g2 = agis.Graph.chung_lu(ctx, n, 2.1, 32.0, seed=3)
+    o2, c2 = g2.csr()
+    assert (o2 == off).all() and (c2 == cols).all()
