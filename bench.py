@@ -56,6 +56,10 @@ def parse_args():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--json-out", default="")
+    ap.add_argument("--batch64", action="store_true",
+                    help="also run the batching configuration: R-MAT scale 24 built on the device, 64 "
+                         "queries with budgets 2^16..2^26, one autotuned persistent launch vs 64 plain launches")
+    ap.add_argument("--batch-scale", type=int, default=24)
     ap.add_argument("--serve", action="store_true",
                     help="also run the serving load (saturation, then Poisson at 50/80/95%%)")
     ap.add_argument("--serve-seconds", type=float, default=15.0)
@@ -343,6 +347,47 @@ def serve_load(agis, g, seconds, seed=7, max_slots=64, budget=200 << 30, burst=6
     return out
 
 
+# ------------------------------------------------------------------ batching configuration
+
+def batch64(agis, ctx, scale, stream):
+    """64 pattern queries (cliques, cycles, paths, stars of 3-7 vertices, tailed
+    triangle, diamond, chordal 5-cycle) with fixed trial budgets log-uniform in
+    2^16..2^26 on an R-MAT graph generated on the device: all of them in one
+    persistent launch (after the grid autotuner) against 64 plain launches."""
+    import torch
+    from paper_2601_01388_b300 import inputs as I
+    t0 = time.perf_counter()
+    g = agis.Graph.rmat(ctx, scale, 16, 0.57, 0.19, 0.19, seed=1)
+    t_gen = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    g.preprocess(1, CMIN)
+    t_prep = time.perf_counter() - t0
+    qs = I.batch_queries(64, seed=1)
+    pats = [agis.Pattern(*pat) for _, pat, _ in qs]
+    opts = [agis.default_opts(mode=0, seed=500 + i, eps=0.0, max_trials=b) for i, (_, _, b) in enumerate(qs)]
+    t0 = time.perf_counter()
+    for p, o in zip(pats, opts):
+        agis.prepare(g, p, o)
+    t_tables = time.perf_counter() - t0
+    best = agis.autotune(g, pats, opts, 1 << 15)
+    total = sum(b for _, _, b in qs)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plain = [agis.estimate(g, p, o) for p, o in zip(pats, opts)]
+    t_plain = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    batched = agis.estimate_batch(g, pats, opts)
+    t_batch = time.perf_counter() - t0
+    same = all(a["sum_x"] == b["sum_x"] and a["hits"] == b["hits"] for a, b in zip(plain, batched))
+    info = g.info()
+    g.close()
+    return {"graph": f"R-MAT scale {scale} (device), nv {info['nv']}, nnz {info['nnz']}, max degree {info['max_degree']}",
+            "generate_s": t_gen, "preprocess_s": t_prep, "tables_s": t_tables, "queries": len(qs),
+            "trials": total, "autotuned_ctas_per_sm": best, "plain_s": t_plain, "batched_s": t_batch,
+            "plain_samples_per_s": total / t_plain, "batched_samples_per_s": total / t_batch,
+            "same_results": same}
+
+
 # ------------------------------------------------------------------ GPU arm
 
 def run_gpu(args, world, rank, local):
@@ -529,6 +574,10 @@ def run_gpu(args, world, rank, local):
                             "converged": r["converged"]})
             tte["uniform_plain"] = uni
 
+        batching = None
+        if args.batch64:
+            batching = batch64(agis, ctx, args.batch_scale, stream)
+
         serving = None
         if args.serve:
             serving = serve_load(agis, g, args.serve_seconds)
@@ -570,6 +619,8 @@ def run_gpu(args, world, rank, local):
     }
     if serving is not None:
         line["serving"] = serving
+    if batching is not None:
+        line["batch64"] = batching
     return line
 
 

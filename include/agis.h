@@ -45,7 +45,7 @@ typedef enum {
     AGIS_ERR_CUDA = -3,     /* a CUDA runtime call failed (no device, launch error ...) */
     AGIS_ERR_GRAPH = -4,    /* CSR violates the conventions above                       */
     AGIS_ERR_PATTERN = -5,  /* pattern violates the conventions above                   */
-    AGIS_ERR_TIMEOUT = -6,  /* a bounded device loop hit its iteration cap              */
+    AGIS_ERR_TIMEOUT = -6,  /* reserved: no device loop of this library waits on another agent */
     AGIS_ERR_BUSY = -7,     /* server: result not ready yet, or admission refused       */
     AGIS_ERR_STATE = -8     /* call not valid in the handle's current state             */
 } agis_status;
@@ -197,8 +197,8 @@ int agis_pattern_free(agis_pattern *p);
  * (seed, 0)) in tiles of 1024 on the device, and evaluates Alg. 1 on host at every
  * chunk_trials checkpoint once min_trials trials are in.  The result is that of the
  * first converged checkpoint, or of max_trials; it is a deterministic function of
- * (graph, pattern, opts).  eps <= 0 runs exactly max_trials (rounded up to 1024).
- * Errors: ARG, STATE (graph not preprocessed), NOMEM, CUDA, TIMEOUT. */
+ * (graph, pattern, opts).  eps <= 0 runs exactly max_trials trials.
+ * Errors: ARG, STATE (graph not preprocessed), NOMEM, CUDA. */
 int agis_estimate(agis_graph *g, const agis_pattern *p, const agis_opts *opts,
                   agis_result *out);
 

@@ -741,6 +741,88 @@ int64_t orc_bruteforce_count(int64_t nv, const int64_t *off, const int32_t *cols
     return (int64_t)bf_rec(nv, off, cols, k, adj, map, 0);
 }
 
+/* Exact embedding counts for three small patterns on graphs too large for the
+ * backtracking counter, by the classical identities (each pinned to brute force on
+ * tiny graphs by the tests):
+ *   triangle: C = sum over ordered adjacent (u, v) of |N(u) & N(v)|;
+ *   4-cycle:  C = sum over ordered a != c of w(a,c) (w(a,c) - 1), w = |N(a) & N(c)|
+ *             (u0 = a, u2 = c, then an ordered pair of distinct common neighbours);
+ *   4-clique: C = 24 * #K4, #K4 counted over id-increasing vertex quadruples. */
+static int64_t common_count(const int64_t *off, const int32_t *cols, int32_t a, int32_t b)
+{
+    int64_t i = off[a], j = off[b], c = 0;
+    while (i < off[a + 1] && j < off[b + 1]) {
+        if (cols[i] < cols[j]) i++;
+        else if (cols[i] > cols[j]) j++;
+        else { c++; i++; j++; }
+    }
+    return c;
+}
+
+int64_t orc_exact_triangle(int64_t nv, const int64_t *off, const int32_t *cols)
+{
+    int64_t total = 0;
+    for (int64_t u = 0; u < nv; ++u)
+        for (int64_t e = off[u]; e < off[u + 1]; ++e)
+            total += common_count(off, cols, (int32_t)u, cols[e]);
+    return total;
+}
+
+int64_t orc_exact_4cycle(int64_t nv, const int64_t *off, const int32_t *cols)
+{
+    int64_t *w = (int64_t *)calloc((size_t)nv, sizeof(int64_t));
+    int32_t *touched = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nv > 0 ? nv : 1));
+    if (!w || !touched) { free(w); free(touched); return -1; }
+    int64_t total = 0;
+    for (int64_t a = 0; a < nv; ++a) {
+        int64_t nt = 0;
+        for (int64_t e = off[a]; e < off[a + 1]; ++e) {
+            int32_t b = cols[e];
+            for (int64_t f = off[b]; f < off[b + 1]; ++f) {
+                int32_t c = cols[f];
+                if (c == a) continue;
+                if (w[c] == 0) touched[nt++] = c;
+                w[c]++;
+            }
+        }
+        for (int64_t t = 0; t < nt; ++t) {
+            int64_t x = w[touched[t]];
+            total += x * (x - 1);
+            w[touched[t]] = 0;
+        }
+    }
+    free(w);
+    free(touched);
+    return total;
+}
+
+int64_t orc_exact_4clique(int64_t nv, const int64_t *off, const int32_t *cols)
+{
+    int64_t k4 = 0;
+    int32_t *t = NULL;
+    int64_t cap = 0;
+    for (int64_t u = 0; u < nv; ++u) {
+        for (int64_t e = off[u]; e < off[u + 1]; ++e) {
+            int32_t v = cols[e];
+            if (v <= u) continue;
+            /* T = common neighbours of u and v above v */
+            int64_t need = off[u + 1] - off[u];
+            if (need > cap) { free(t); cap = need; t = (int32_t *)malloc(sizeof(int32_t) * (size_t)cap); if (!t) return -1; }
+            int64_t n = 0, i = off[u], j = off[v];
+            while (i < off[u + 1] && j < off[v + 1]) {
+                if (cols[i] < cols[j]) i++;
+                else if (cols[i] > cols[j]) j++;
+                else { if (cols[i] > v) t[n++] = cols[i]; i++; j++; }
+            }
+            for (int64_t x = 0; x < n; ++x)
+                for (int64_t y = x + 1; y < n; ++y)
+                    k4 += is_neighbour(off, cols, t[x], t[y]);
+        }
+    }
+    free(t);
+    return 24 * k4;
+}
+
 /* Exact first and second moments of the sampler output by walking every branch of
  * Alg. 3 with its probability q(v)/W (Thm. 2 says E[X] = C(G,P)).  Also counts the
  * successful trajectories. */

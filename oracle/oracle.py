@@ -92,6 +92,9 @@ def lib():
         L.orc_bruteforce_count.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_int32,
                                            C.c_int32, P(C.c_int32)]
         L.orc_bruteforce_count.restype = C.c_int64
+        for fn in ("orc_exact_triangle", "orc_exact_4cycle", "orc_exact_4clique"):
+            getattr(L, fn).argtypes = [C.c_int64, C.c_void_p, C.c_void_p]
+            getattr(L, fn).restype = C.c_int64
         L.orc_enumerate.argtypes = [C.c_void_p, P(C.c_double), P(C.c_double), P(C.c_uint64)]
         L.orc_trajectory_prob.argtypes = [C.c_void_p, P(C.c_int32)]
         L.orc_trajectory_prob.restype = C.c_double
@@ -204,6 +207,14 @@ def bruteforce_count(off, cols, k, edges):
     cols = np.ascontiguousarray(cols, dtype=np.int32)
     flat, p = _edges_arr(edges)
     return int(lib().orc_bruteforce_count(len(off) - 1, _ptr(off), _ptr(cols), k, len(flat) // 2, p))
+
+
+def exact_count(off, cols, name):
+    """Exact C(G,P) for the triangle, 4-cycle or 4-clique on a larger graph."""
+    off = np.ascontiguousarray(off, dtype=np.int64)
+    cols = np.ascontiguousarray(cols, dtype=np.int32)
+    fn = {"triangle": "orc_exact_triangle", "4-cycle": "orc_exact_4cycle", "4-clique": "orc_exact_4clique"}[name]
+    return int(getattr(lib(), fn)(len(off) - 1, _ptr(off), _ptr(cols)))
 
 
 class Query:

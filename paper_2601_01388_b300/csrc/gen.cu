@@ -268,7 +268,8 @@ int build_csr(agis_ctx *ctx, const Src &src, uint64_t nv, agis_graph **out)
     cudaFree(keys2); keys2 = nullptr;
     cudaFree(temp); temp = nullptr;
     // trim cols to the exact size
-    if (cudaMalloc(&g->cols, sizeof(int32_t) * std::max<int64_t>(written, 1)) != cudaSuccess) return fail(AGIS_ERR_NOMEM);
+    // 16 entries of padding: the sampler's 16-byte row loads may read past the end
+    if (cudaMalloc(&g->cols, sizeof(int32_t) * (size_t)(written + 16)) != cudaSuccess) return fail(AGIS_ERR_NOMEM);
     if (written > 0 && cudaMemcpyAsync(g->cols, cols_tmp, sizeof(int32_t) * written, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
         return fail(AGIS_ERR_CUDA);
     if (cudaStreamSynchronize(st) != cudaSuccess) return fail(AGIS_ERR_CUDA);

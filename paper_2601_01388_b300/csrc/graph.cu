@@ -482,7 +482,8 @@ extern "C" int agis_graph_load_csr(agis_ctx *ctx, const void *offsets, int offse
     g->nnz = nnz;
     auto fail = [&](int rc) { cudaFree(g->off); cudaFree(g->cols); delete g; return rc; };
     if (cudaMalloc(&g->off, sizeof(int64_t) * (size_t)(nv + 1)) != cudaSuccess) return fail(AGIS_ERR_NOMEM);
-    if (cudaMalloc(&g->cols, sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1)) != cudaSuccess)
+    // 16 entries of padding: the sampler's 16-byte row loads may read past the end
+    if (cudaMalloc(&g->cols, sizeof(int32_t) * (size_t)(nnz + 16)) != cudaSuccess)
         return fail(AGIS_ERR_NOMEM);
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     if (offsets_are_64bit) {

@@ -130,22 +130,23 @@ size_t scratch_stride(uint32_t cap)
 }
 
 // Per-warp candidate-list scratch for a launch of `grid` CTAs: lists as long as
-// the largest row, at most 16384 entries and within an eighth of device memory
-// (longer anchor rows take the sampler's list-free path).
+// the largest row, at most 65536 entries and within an eighth of device memory
+// (a step whose survivors overflow takes the sampler's list-free path).  The
+// allocation is padded so that 16-byte list loads may read past a list's end.
 int ensure_scratch(agis_graph *g, LaunchBuffers &lb, int grid)
 {
     if (lb.d_scratch && lb.scratch_grid >= grid) return AGIS_OK;
     size_t free_b = 0, total_b = 0;
     AGIS_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
     const size_t warps = (size_t)grid * kWarps;
-    uint64_t cap = (uint64_t)std::min<int64_t>(std::max<int64_t>(g->max_deg, 64), 16384);
+    uint64_t cap = (uint64_t)std::min<int64_t>(std::max<int64_t>(g->max_deg, 64), 65536);
     cap = (cap + 63) / 64 * 64;
     const size_t budget = total_b / 8;
     while (cap > 64 && scratch_stride((uint32_t)cap) * warps > budget) cap = (cap / 2 + 63) / 64 * 64;
     cudaFree(lb.d_scratch);
     lb.d_scratch = nullptr;
     lb.scratch_bytes = 0;
-    AGIS_CUDA_TRY(cudaMalloc(&lb.d_scratch, scratch_stride((uint32_t)cap) * warps));
+    AGIS_CUDA_TRY(cudaMalloc(&lb.d_scratch, scratch_stride((uint32_t)cap) * warps + 256));
     lb.scratch_bytes = scratch_stride((uint32_t)cap) * warps;
     lb.scratch_cap = (uint32_t)cap;
     lb.scratch_grid = grid;

@@ -288,8 +288,12 @@ __device__ __forceinline__ void emit_window(bool ok, int32_t x, uint64_t w, int3
 // otherwise it is found either by a warp merge (R read once, 32 entries per
 // coalesced load, each loaded entry located among the 32 list entries of the window
 // by a shuffle search) or by one binary search per list entry, whichever the sizes
-// make cheaper.  The bitmap and no-row cases run four windows at a time so that
-// four list loads, four bit tests and four weight gathers are in flight together.
+// make cheaper.
+#ifndef AGIS_FILTER_GROUPS
+#define AGIS_FILTER_GROUPS 2
+#endif
+constexpr int kGroups = AGIS_FILTER_GROUPS;
+
 template <bool kWeigh>
 __device__ uint32_t filter_list(const int32_t *L, uint32_t n, const int32_t *R, int64_t m,
                                 const uint32_t *Rbits, const int32_t *tau_s, int tau_n, int32_t *out,
@@ -299,29 +303,81 @@ __device__ uint32_t filter_list(const int32_t *L, uint32_t n, const int32_t *R, 
     uint32_t cnt = 0;
     uint64_t carry = 0;
     if (Rbits || !R) {
-        constexpr int U = 4;
-        for (uint32_t base = 0; base < n; base += 32 * U) {
-            int32_t x[U];
-            bool ok[U];
+        // Survivor ids first: 16-byte loads of four consecutive entries per lane,
+        // kGroups groups of 128 entries per iteration, so 4 * kGroups bitmap probes
+        // per lane are in flight together; the survivors' weights are gathered afterwards in
+        // a pass over the (shorter) survivor list.  Loads start at the 16-byte
+        // block holding L[0] and may read up to three entries past L[n-1] (the row
+        // and list buffers are padded for that); such entries are masked out.
+        const uint32_t mis = (uint32_t)(((uintptr_t)L & 15u) >> 2);
+        const int32_t *La = L - mis;
+        const uint32_t total = n + mis;
+        for (uint32_t base = 0; base < total; base += 128 * kGroups) {
+            int4 v[kGroups];
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const uint32_t idx = base + 32 * u + lane;
-                ok[u] = idx < n;
-                x[u] = ok[u] ? L[idx] : 0;
+            for (int gi = 0; gi < kGroups; ++gi) {
+                const uint32_t k = base + 128 * gi + 4 * lane;
+                v[gi] = k < total ? __ldg(reinterpret_cast<const int4 *>(La + k)) : make_int4(0, 0, 0, 0);
+            }
+            unsigned okm[kGroups];
+#pragma unroll
+            for (int gi = 0; gi < kGroups; ++gi) {
+                const int64_t i0 = (int64_t)(base + 128 * gi + 4 * lane) - mis;
+                const int32_t e4[4] = {v[gi].x, v[gi].y, v[gi].z, v[gi].w};
+                unsigned mk = 0;
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    bool ok = i0 + e >= 0 && i0 + e < (int64_t)n;
+                    for (int j = 0; j < tau_n; ++j) ok = ok && (e4[e] != tau_s[j]);
+                    if (Rbits) ok = ok && bit_test(Rbits, e4[e]);
+                    mk |= (ok ? 1u : 0u) << e;
+                }
+                okm[gi] = mk;
             }
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                for (int j = 0; j < tau_n; ++j) ok[u] = ok[u] && (x[u] != tau_s[j]);
-                if (Rbits) ok[u] = ok[u] && bit_test(Rbits, x[u]);
+            for (int gi = 0; gi < kGroups; ++gi) {
+                const uint32_t c = __popc(okm[gi]);
+                uint32_t incl = c;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t t = __shfl_up_sync(kFull, incl, o);
+                    if (lane >= o) incl += t;
+                }
+                uint32_t pos = cnt + incl - c;
+                const int32_t e4[4] = {v[gi].x, v[gi].y, v[gi].z, v[gi].w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    if ((okm[gi] >> e) & 1u) {
+                        if (pos < cap) out[pos] = e4[e];
+                        ++pos;
+                    }
+                }
+                cnt += __shfl_sync(kFull, incl, 31);
             }
-            uint64_t w[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) w[u] = (kWeigh && ok[u]) ? (approx ? __ldg(q + x[u]) : 1u) : 0u;
-#pragma unroll
-            for (int u = 0; u < U; ++u) emit_window<kWeigh>(ok[u], x[u], w[u], out, out_pw, cap, cnt, carry, lane);
             if (cnt > cap) return cnt;         // list full: the caller takes the list-free path
         }
-        if (kWeigh) *W = carry;
+        if (kWeigh) {
+            __syncwarp();
+            for (uint32_t b = 0; b < cnt; b += 64) {
+                int32_t x[2];
+                uint64_t w[2];
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const uint32_t idx = b + 32 * u + lane;
+                    x[u] = idx < cnt ? out[idx] : 0;
+                }
+#pragma unroll
+                for (int u = 0; u < 2; ++u)
+                    w[u] = (b + 32 * u + lane < cnt) ? (approx ? __ldg(q + x[u]) : 1u) : 0u;
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const uint64_t incl = warp_incl_scan(w[u], lane);
+                    const uint32_t idx = b + 32 * u + lane;
+                    if (idx < cnt) out_pw[idx] = carry + incl;
+                    carry += __shfl_sync(kFull, incl, 31);
+                }
+            }
+            *W = carry;
+        }
         return cnt;
     }
     int lg = 1;

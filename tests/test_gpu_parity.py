@@ -235,3 +235,33 @@ def test_bad_opts_rejected(agis, graphs):
     with pytest.raises(agis.AgisError) as e:
         agis.estimate(g, agis.Pattern(*I.PATTERNS["triangle"]), agis.default_opts(chunk_trials=1000))
     assert e.value.status == agis.ERR_ARG
+
+
+# ------------------------------------------------------------------ small configuration
+
+@pytest.fixture(scope="module")
+def rmat14(agis, ctx, oracle_mod):
+    off, cols = I.rmat_graph(14, 16, 0.57, 0.19, 0.19, seed=1)
+    g = make_graph(agis, ctx, off, cols)
+    nsum, hits = oracle_mod.graph_stats(off, cols, 1)
+    return off, cols, g, nsum, hits
+
+
+@pytest.mark.parametrize("name", ["triangle", "4-cycle", "4-clique"])
+@pytest.mark.parametrize("mode", [1, 2])
+def test_scale14_estimates_cover_exact_counts(agis, oracle_mod, rmat14, name, mode):
+    """R-MAT scale 14, 2^20 trials under f_approx (mode 1) and f_uniform (mode 2),
+    Philox seed 1: the estimate lies within 4 standard errors of the exact count,
+    and a prefix of the trials matches the oracle."""
+    off, cols, g, nsum, hits = rmat14
+    k, edges = I.PATTERNS[name]
+    n = 1 << 20
+    r = agis.estimate(g, agis.Pattern(k, edges), agis.default_opts(mode=mode, seed=1, eps=0.0, max_trials=n))
+    truth = oracle_mod.exact_count(off, cols, name)
+    se = (r["var"] / n) ** 0.5
+    assert abs(r["estimate"] - truth) <= 4 * se + 1e-9 * truth, (r["estimate"], truth, se)
+    q = oracle_mod.Query(off, cols, k, edges, nsum=nsum, hits=hits, c_min=CMIN, mode=mode, seed=1)
+    s = q.sums(0, 8192)
+    part = agis.estimate(g, agis.Pattern(k, edges), agis.default_opts(mode=mode, seed=1, eps=0.0, max_trials=8192))
+    assert part["hits"] == s["hits"] and part["sectors"] == s["sectors"]
+    assert part["sum_x"] == pytest.approx(s["sum_x"], rel=REL, abs=0)

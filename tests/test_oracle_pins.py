@@ -491,3 +491,18 @@ def test_min_trials_gate(oracle_mod):
     assert r["converged"] == 1 and r["trials"] == 256
     r = q.estimate(eps=0.01, delta=0.05, chunk=64, min_trials=64, max_trials=4096)
     assert r["trials"] == 64
+
+
+@pytest.mark.parametrize("gname", sorted(TINY_GRAPHS))
+def test_exact_counters_match_bruteforce(oracle_mod, gname):
+    off, cols = TINY_GRAPHS[gname]()
+    for name in ("triangle", "4-cycle", "4-clique"):
+        k, edges = I.PATTERNS[name]
+        assert oracle_mod.exact_count(off, cols, name) == oracle_mod.bruteforce_count(off, cols, k, edges)
+
+
+def test_exact_counters_on_rmat_match_bruteforce(oracle_mod):
+    off, cols = I.rmat_graph(7, 8, seed=2)
+    for name in ("triangle", "4-cycle", "4-clique"):
+        k, edges = I.PATTERNS[name]
+        assert oracle_mod.exact_count(off, cols, name) == oracle_mod.bruteforce_count(off, cols, k, edges)
