@@ -60,6 +60,10 @@ def parse_args():
                     help="also run the batching configuration: R-MAT scale 24 built on the device, 64 "
                          "queries with budgets 2^16..2^26, one autotuned persistent launch vs 64 plain launches")
     ap.add_argument("--batch-scale", type=int, default=24)
+    ap.add_argument("--large", action="store_true",
+                    help="also run the large-graph configuration: R-MAT scale 28, edge factor 32, built on the "
+                         "device; 6-clique and 7-cycle to +-1%% under f_approx and f_uniform (2^30-trial budget)")
+    ap.add_argument("--large-scale", type=int, default=28)
     ap.add_argument("--serve", action="store_true",
                     help="also run the serving load (saturation, then Poisson at 50/80/95%%)")
     ap.add_argument("--serve-seconds", type=float, default=15.0)
@@ -388,6 +392,45 @@ def batch64(agis, ctx, scale, stream):
             "same_results": same}
 
 
+# ------------------------------------------------------------------ large graph
+
+def large_graph(agis, ctx, scale):
+    """R-MAT scale 28 with edge factor 32 built on the device (int64 offsets, int32
+    columns); time to +-1% at 95% confidence for the 6-clique and the 7-cycle under
+    f_approx (D^pi) and f_uniform, at most 2^30 trials each.  Row prefixes are kept
+    to the highest-degree rows within 24 GB per configuration."""
+    import torch
+    from paper_2601_01388_b300 import inputs as I
+    t0 = time.perf_counter()
+    g = agis.Graph.rmat(ctx, scale, 32, 0.57, 0.19, 0.19, seed=1)
+    t_gen = time.perf_counter() - t0
+    g.set_memory_policy(row_prefix_bytes=24 << 30)
+    t0 = time.perf_counter()
+    g.preprocess(1, CMIN)
+    t_prep = time.perf_counter() - t0
+    info = g.info()
+    out = {"graph": f"R-MAT scale {scale} edge factor 32 (device): nv {info['nv']}, nnz {info['nnz']}, "
+                    f"max degree {info['max_degree']}", "generate_s": t_gen, "preprocess_s": t_prep, "runs": []}
+    for name in ("6-clique", "7-cycle"):
+        p = agis.Pattern(*I.PATTERNS[name])
+        for mode, label in ((0, "f_approx (D^pi)"), (2, "f_uniform")):
+            o = agis.default_opts(mode=mode, seed=7, eps=0.01, delta=0.05, chunk_trials=1 << 16,
+                                  min_trials=1 << 16, max_trials=1 << 30)
+            t1 = time.perf_counter()
+            agis.prepare(g, p, o)
+            t_tab = time.perf_counter() - t1
+            t1 = time.perf_counter()
+            r = agis.estimate(g, p, o)
+            dt = time.perf_counter() - t1
+            out["runs"].append({"pattern": name, "distribution": label, "tables_s": t_tab, "s": dt,
+                                "trials": r["trials"], "converged": r["converged"], "estimate": r["estimate"],
+                                "eps_hat": r["eps_hat"], "samples_per_s": r["trials"] / dt})
+    out["device_bytes"] = g.info()["device_bytes"]
+    g.close()
+    torch.cuda.empty_cache()
+    return out
+
+
 # ------------------------------------------------------------------ GPU arm
 
 def run_gpu(args, world, rank, local):
@@ -574,6 +617,10 @@ def run_gpu(args, world, rank, local):
                             "converged": r["converged"]})
             tte["uniform_plain"] = uni
 
+        large = None
+        if args.large:
+            large = large_graph(agis, ctx, args.large_scale)
+
         batching = None
         if args.batch64:
             batching = batch64(agis, ctx, args.batch_scale, stream)
@@ -621,6 +668,8 @@ def run_gpu(args, world, rank, local):
         line["serving"] = serving
     if batching is not None:
         line["batch64"] = batching
+    if large is not None:
+        line["large_graph"] = large
     return line
 
 

@@ -139,7 +139,8 @@ int agis_graph_weight_table(agis_graph *g, const int32_t cfg[4], uint64_t *q,
                             uint64_t *prefix, int32_t *shift);
 
 /* agis_graph_row_prefix: copies the per-row inclusive running sums of q over each
- * row's neighbours for configuration cfg (nnz uint64, caller-owned host array). */
+ * row's neighbours for configuration cfg (nnz uint64, caller-owned host array).
+ * STATE when the memory policy only allows a partial table. */
 int agis_graph_row_prefix(agis_graph *g, const int32_t cfg[4], uint64_t *row_prefix);
 
 /* agis_graph_validate: re-checks the CSR conventions above on the device (e.g. for a
@@ -149,6 +150,19 @@ int agis_graph_validate(agis_graph *g);
 /* agis_graph_copy_csr: copies the device CSR to caller-owned host arrays off[nv+1]
  * (int64) and cols[nnz] (int32); either may be NULL. */
 int agis_graph_copy_csr(const agis_graph *g, int64_t *off, int32_t *cols);
+
+/* agis_graph_set_memory_policy: device-memory budgets of the optional structures
+ * that speed up sampling (0 keeps a setting): row_prefix_bytes -- the largest
+ * per-configuration row-prefix table built in full (default a quarter of device
+ * memory); past it only the highest-degree rows that fit get a prefix and the
+ * other single-backward draws scan their row; bitmap_bytes -- total for hub
+ * neighbour bitmaps (default a sixteenth), built for vertices of degree at least
+ * bitmap_min_degree (default 1024) at the next agis_graph_preprocess;
+ * list_entries (>= 64) -- per-warp candidate-list capacity (default 65536), whose
+ * overflow makes a step take the list-free scan.  Results never depend on these
+ * settings.  Cached weight tables not in use are dropped.  Errors: ARG. */
+int agis_graph_set_memory_policy(agis_graph *g, uint64_t row_prefix_bytes, uint64_t bitmap_bytes,
+                                 int64_t bitmap_min_degree, uint32_t list_entries);
 
 /* agis_graph_drop_tables: frees every cached weight table (they are rebuilt on
  * demand). */

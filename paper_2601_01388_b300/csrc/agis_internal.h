@@ -29,7 +29,9 @@ constexpr uint64_t kStreamCC = 2;    // ... of a clustering-coefficient probe
 struct DevStep {
     int32_t nb;                 // |B[i]|: number of backward neighbours
     int16_t approx;             // D(i): 1 = f_approx, 0 = f_uniform
-    int16_t inc;                // backward set = previous step's plus the previous vertex
+    int8_t inc;                 // backward set = previous step's plus the previous vertex
+    int8_t rp_mode;             // pref for |B| = 1: 0 none, 1 per-row prefix of every row,
+                                // 2 prefix of high-degree rows only (located by rp_base)
     int8_t back[kMaxK];         // step indices of the backward neighbours
     const uint64_t *q;          // quantised f_approx weight per vertex (approx only)
     const uint64_t *pref;       // step 0: inclusive prefix over vertices; |B| = 1: row prefix
@@ -69,6 +71,7 @@ struct GraphView {
     const int32_t *hub_id;      // per vertex: index of its neighbour bitmap, -1 if none
     const uint32_t *hub_bits;   // bitmaps, hub_words 32-bit words each
     int64_t hub_words;
+    const int64_t *rp_base;     // per vertex: start of its row in partial row-prefix tables, -1 if none
 };
 
 struct WeightTable {
@@ -76,7 +79,9 @@ struct WeightTable {
     int32_t shift = 0;
     uint64_t *q = nullptr;      // nv
     uint64_t *pref = nullptr;   // nv, inclusive prefix over vertices (|B| = 0 configs)
-    uint64_t *rowp = nullptr;   // nnz, inclusive prefix inside each row (|B| = 1 configs)
+    uint64_t *rowp = nullptr;   // inclusive prefix inside each row (|B| = 1 configs): nnz
+                                // entries, or only the rows of g->rp_base when rowp_partial
+    bool rowp_partial = false;
     uint64_t total = 0;
     size_t bytes = 0;
     uint64_t last_use = 0;
@@ -148,7 +153,15 @@ struct agis_graph {
     uint64_t use_clock = 0;
     std::recursive_mutex mu;
     agis::LaunchBuffers lb;     // used by estimate/batch/dump (under mu)
-    size_t rowp_budget = 0;     // largest row-prefix table built (bytes); beyond it draws scan rows
+    // memory policy (agis_graph_set_memory_policy)
+    size_t rowp_budget = 0;     // largest row-prefix table built in full; beyond it only high-degree rows
+    size_t bitmap_budget = 0;   // total bytes of hub neighbour bitmaps (0: a sixteenth of device memory)
+    int64_t bitmap_min_degree = 1024;
+    uint32_t list_cap = 65536;  // per-warp candidate-list capacity
+    // partial row-prefix layout shared by every configuration (built on demand)
+    int64_t *rp_base = nullptr; // per vertex, -1 if its row has no prefix
+    int32_t *rp_rows = nullptr; // the vertices whose rows have one
+    int64_t rp_nrows = 0, rp_entries = 0, rp_min_degree = 0;
     // neighbour bitmaps of the highest-degree vertices (built by preprocessing)
     int32_t *hub_id = nullptr;
     uint32_t *hub_bits = nullptr;
@@ -161,6 +174,8 @@ namespace agis {
 
 // graph.cu
 int build_hub_bitmaps(agis_graph *g);
+int build_partial_rowp_layout(agis_graph *g);
+bool rowp_full_fits(const agis_graph *g);
 int inclusive_scan_u64(agis_ctx *ctx, const uint64_t *in, int64_t n, uint64_t *out);
 int build_weight_table(agis_graph *g, const int32_t cfg[4], bool need_pref, bool need_rowp,
                        WeightTable **out);

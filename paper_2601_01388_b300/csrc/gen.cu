@@ -181,9 +181,11 @@ int build_csr(agis_ctx *ctx, const Src &src, uint64_t nv, agis_graph **out)
 {
     cudaStream_t st = ctx->stream;
     const int gen_blocks = ctx->sm_count * 8;
-    // row chunks small enough that each holds at most 2^30 keys (CUB's int sizes)
+    // row chunks small enough that each holds at most 1.5 * 2^30 keys (CUB takes int
+    // sizes); every chunk re-draws all edges, so fewer, larger chunks are cheaper
+    const uint64_t kChunkKeys = 3ull << 29;
     uint64_t nchunks = 1;
-    while ((2 * src.m) / nchunks > (1ull << 30) && nchunks < nv) nchunks *= 2;
+    while ((2 * src.m) / nchunks > kChunkKeys && nchunks < nv) nchunks *= 2;
     std::vector<unsigned long long> per_chunk;
     uint64_t rows_per_chunk = 0;
     for (;;) {
@@ -200,7 +202,7 @@ int build_csr(agis_ctx *ctx, const Src &src, uint64_t nv, agis_graph **out)
         if (e != cudaSuccess) return AGIS_ERR_CUDA;
         uint64_t mx = 0;
         for (auto x : per_chunk) mx = std::max<uint64_t>(mx, x);
-        if (mx <= (1ull << 30) || nchunks >= nv) break;
+        if (mx <= kChunkKeys || nchunks >= nv) break;
         nchunks *= 2;
     }
     uint64_t cap = 0, upper = 0;

@@ -285,6 +285,31 @@ __global__ void k_row_prefix(const int64_t *off, const int32_t *cols, int64_t nv
     }
 }
 
+// Row prefix of the listed rows only: row of rows[h] goes to out[base[rows[h]] ...].
+__global__ void k_row_prefix_partial(const int64_t *off, const int32_t *cols, const int32_t *rows, int64_t nrows,
+                                     const int64_t *base, const uint64_t *q, uint64_t *out)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t h = warp; h < nrows; h += nwarps) {
+        const int32_t v = rows[h];
+        const int64_t s = off[v], e = off[v + 1];
+        uint64_t *dst = out + base[v];
+        uint64_t carry = 0;
+        for (int64_t i0 = s; i0 < e; i0 += 32) {
+            const int64_t i = i0 + lane;
+            uint64_t w = i < e ? __ldg(q + __ldg(cols + i)) : 0;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint64_t n = __shfl_up_sync(kFull, w, o);
+                if (lane >= o) w += n;
+            }
+            if (i < e) dst[i - s] = carry + w;
+            carry += __shfl_sync(kFull, w, 31);
+        }
+    }
+}
+
 int grid_stride_blocks(const agis_graph *g, int64_t work, int threads)
 {
     int64_t blocks = (work + threads - 1) / threads;
@@ -319,9 +344,10 @@ int inclusive_scan_u64(agis_ctx *ctx, const uint64_t *in, int64_t n, uint64_t *o
 }
 
 
-// Bitmaps for every vertex of degree >= max(1024, t), t the smallest degree whose
-// hub set fits a sixteenth of device memory (nv bits per hub).  A membership test
-// against such a row is then one independent load.
+// Bitmaps for every vertex of degree >= max(bitmap_min_degree, t), t the smallest
+// degree whose hub set fits the bitmap budget (default a sixteenth of device
+// memory; nv bits per hub).  A membership test against such a row is then one
+// independent load.
 int build_hub_bitmaps(agis_graph *g)
 {
     cudaStream_t st = g->ctx->stream;
@@ -338,9 +364,10 @@ int build_hub_bitmaps(agis_graph *g)
     size_t free_b = 0, total_b = 0;
     AGIS_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
     const size_t per_hub = sizeof(uint32_t) * (size_t)g->hub_words;
-    const size_t max_hubs = std::min<size_t>((total_b / 16) / per_hub, 1u << 20);
+    const size_t budget = g->bitmap_budget ? g->bitmap_budget : total_b / 16;
+    const size_t max_hubs = std::min<size_t>(budget / per_hub, 1u << 20);
     std::vector<int64_t> sorted(deg);
-    int64_t t = 1024;
+    int64_t t = std::max<int64_t>(1, g->bitmap_min_degree);
     if (sorted.size() > max_hubs && max_hubs > 0) {
         std::nth_element(sorted.begin(), sorted.begin() + (max_hubs - 1), sorted.end(), std::greater<int64_t>());
         t = std::max<int64_t>(t, sorted[max_hubs - 1] + 1);
@@ -369,6 +396,46 @@ int build_hub_bitmaps(agis_graph *g)
     AGIS_CUDA_TRY(cudaStreamSynchronize(st));
     g->n_hubs = (int64_t)hubs.size();
     g->lb.generation++;          // a captured epoch graph holds the old bitmap addresses
+    return AGIS_OK;
+}
+
+bool rowp_full_fits(const agis_graph *g) { return (size_t)g->nnz * sizeof(uint64_t) <= g->rowp_budget; }
+
+// Rows that get a prefix when the full table does not fit: the highest-degree rows
+// whose entries fit the row-prefix budget (shared by every configuration).
+int build_partial_rowp_layout(agis_graph *g)
+{
+    if (g->rp_base) return AGIS_OK;
+    cudaStream_t st = g->ctx->stream;
+    std::vector<int64_t> off((size_t)g->nv + 1);
+    AGIS_CUDA_TRY(cudaMemcpy(off.data(), g->off, sizeof(int64_t) * off.size(), cudaMemcpyDeviceToHost));
+    std::vector<int32_t> order((size_t)g->nv);
+    for (int64_t v = 0; v < g->nv; ++v) order[(size_t)v] = (int32_t)v;
+    auto deg = [&](int32_t v) { return off[(size_t)v + 1] - off[(size_t)v]; };
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return deg(a) > deg(b); });
+    const int64_t cap_entries = (int64_t)(g->rowp_budget / sizeof(uint64_t));
+    std::vector<int64_t> base((size_t)g->nv, -1);
+    std::vector<int32_t> rows;
+    int64_t used = 0, min_deg = 0;
+    for (int32_t v : order) {
+        const int64_t d = deg(v);
+        if (d == 0 || used + d > cap_entries) break;
+        base[(size_t)v] = used;
+        rows.push_back(v);
+        used += d;
+        min_deg = d;
+    }
+    AGIS_CUDA_TRY(cudaMalloc(&g->rp_base, sizeof(int64_t) * (size_t)g->nv));
+    AGIS_CUDA_TRY(cudaMemcpyAsync(g->rp_base, base.data(), sizeof(int64_t) * (size_t)g->nv, cudaMemcpyHostToDevice, st));
+    if (!rows.empty()) {
+        AGIS_CUDA_TRY(cudaMalloc(&g->rp_rows, sizeof(int32_t) * rows.size()));
+        AGIS_CUDA_TRY(cudaMemcpyAsync(g->rp_rows, rows.data(), sizeof(int32_t) * rows.size(), cudaMemcpyHostToDevice, st));
+    }
+    AGIS_CUDA_TRY(cudaStreamSynchronize(st));
+    g->rp_nrows = (int64_t)rows.size();
+    g->rp_entries = used;
+    g->rp_min_degree = min_deg;
+    g->lb.generation++;
     return AGIS_OK;
 }
 
@@ -450,12 +517,28 @@ int build_weight_table(agis_graph *g, const int32_t cfg[4], bool need_pref, bool
         AGIS_CUDA_TRY(cudaStreamSynchronize(st));
     }
     if (need_rowp && !t->rowp) {
-        AGIS_CUDA_TRY(cudaMalloc(&t->rowp, sizeof(uint64_t) * (size_t)(g->nnz > 0 ? g->nnz : 1)));
-        t->bytes += sizeof(uint64_t) * (size_t)g->nnz;
-        const int blocks = grid_stride_blocks(g, g->nv * 32, 256);
-        count_launch();
-        k_row_prefix<<<blocks, 256, 0, st>>>(g->off, g->cols, g->nv, t->q, t->rowp);
-        AGIS_CUDA_TRY(cudaGetLastError());
+        if (rowp_full_fits(g)) {
+            AGIS_CUDA_TRY(cudaMalloc(&t->rowp, sizeof(uint64_t) * (size_t)(g->nnz > 0 ? g->nnz : 1)));
+            t->bytes += sizeof(uint64_t) * (size_t)g->nnz;
+            t->rowp_partial = false;
+            const int blocks = grid_stride_blocks(g, g->nv * 32, 256);
+            count_launch();
+            k_row_prefix<<<blocks, 256, 0, st>>>(g->off, g->cols, g->nv, t->q, t->rowp);
+            AGIS_CUDA_TRY(cudaGetLastError());
+        } else {
+            int rc = build_partial_rowp_layout(g);
+            if (rc != AGIS_OK) return rc;
+            if (g->rp_nrows > 0) {
+                AGIS_CUDA_TRY(cudaMalloc(&t->rowp, sizeof(uint64_t) * (size_t)g->rp_entries));
+                t->bytes += sizeof(uint64_t) * (size_t)g->rp_entries;
+                t->rowp_partial = true;
+                const int blocks = grid_stride_blocks(g, g->rp_nrows * 32, 256);
+                count_launch();
+                k_row_prefix_partial<<<blocks, 256, 0, st>>>(g->off, g->cols, g->rp_rows, g->rp_nrows, g->rp_base,
+                                                             t->q, t->rowp);
+                AGIS_CUDA_TRY(cudaGetLastError());
+            }
+        }
     }
     t->last_use = ++g->use_clock;
     *out = t;
@@ -624,6 +707,7 @@ extern "C" int agis_graph_row_prefix(agis_graph *g, const int32_t cfg[4], uint64
     int rc = build_weight_table(g, cfg, false, true, &t);
     if (rc != AGIS_OK) return rc;
     AGIS_CUDA_TRY(cudaStreamSynchronize(g->ctx->stream));
+    if (!t->rowp || t->rowp_partial) return AGIS_ERR_STATE;
     AGIS_CUDA_TRY(cudaMemcpy(row_prefix, t->rowp, sizeof(uint64_t) * (size_t)g->nnz, cudaMemcpyDeviceToHost));
     return AGIS_OK;
 }
@@ -740,4 +824,32 @@ extern "C" int agis_prefix_sum_u64_noalloc(const uint64_t *in, int64_t n, uint64
     count_launch();
     k_scan_apply<<<(unsigned)tiles, kScanThreads, 0, st>>>(in, n, tile_sums, out);
     return cuda_status(cudaGetLastError());
+}
+
+extern "C" int agis_graph_set_memory_policy(agis_graph *g, uint64_t row_prefix_bytes, uint64_t bitmap_bytes,
+                                            int64_t bitmap_min_degree, uint32_t list_entries)
+{
+    if (!g || bitmap_min_degree < 0 || (list_entries != 0 && list_entries < 64)) return AGIS_ERR_ARG;
+    std::lock_guard<std::recursive_mutex> lk(g->mu);
+    cudaSetDevice(g->ctx->device);
+    cudaStreamSynchronize(g->ctx->stream);
+    if (row_prefix_bytes) g->rowp_budget = (size_t)row_prefix_bytes;
+    if (bitmap_bytes) g->bitmap_budget = (size_t)bitmap_bytes;
+    if (bitmap_min_degree) g->bitmap_min_degree = bitmap_min_degree;
+    if (list_entries) g->list_cap = list_entries;
+    // tables and the partial layout follow the new budget when rebuilt
+    for (auto it = g->tables.begin(); it != g->tables.end();) {
+        if (it->second.pins > 0) { ++it; continue; }
+        free_table(it->second);
+        it = g->tables.erase(it);
+    }
+    if (g->tables.empty()) {
+        cudaFree(g->rp_base);
+        cudaFree(g->rp_rows);
+        g->rp_base = nullptr;
+        g->rp_rows = nullptr;
+        g->rp_nrows = g->rp_entries = g->rp_min_degree = 0;
+    }
+    g->lb.generation++;
+    return AGIS_OK;
 }

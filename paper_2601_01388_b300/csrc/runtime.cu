@@ -135,11 +135,12 @@ size_t scratch_stride(uint32_t cap)
 // allocation is padded so that 16-byte list loads may read past a list's end.
 int ensure_scratch(agis_graph *g, LaunchBuffers &lb, int grid)
 {
-    if (lb.d_scratch && lb.scratch_grid >= grid) return AGIS_OK;
+    const uint64_t want = ((uint64_t)std::min<int64_t>(std::max<int64_t>(g->max_deg, 64), (int64_t)g->list_cap) + 63) / 64 * 64;
+    if (lb.d_scratch && lb.scratch_grid >= grid && lb.scratch_cap <= want && lb.scratch_cap + 64 > want) return AGIS_OK;
     size_t free_b = 0, total_b = 0;
     AGIS_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
     const size_t warps = (size_t)grid * kWarps;
-    uint64_t cap = (uint64_t)std::min<int64_t>(std::max<int64_t>(g->max_deg, 64), 65536);
+    uint64_t cap = (uint64_t)std::min<int64_t>(std::max<int64_t>(g->max_deg, 64), (int64_t)g->list_cap);
     cap = (cap + 63) / 64 * 64;
     const size_t budget = total_b / 8;
     while (cap > 64 && scratch_stride((uint32_t)cap) * warps > budget) cap = (cap / 2 + 63) / 64 * 64;
@@ -176,14 +177,15 @@ int make_dev_query(agis_graph *g, const agis_pattern *p, const agis_opts *o, Dev
             unsigned mi = 0, mp = 0;
             for (int j = 0; j < p->nback[i]; ++j) mi |= 1u << p->back[i][j];
             for (int j = 0; j < p->nback[i - 1]; ++j) mp |= 1u << p->back[i - 1][j];
-            s.inc = (int16_t)(mi == (mp | (1u << (i - 1))) ? 1 : 0);
+            s.inc = (int8_t)(mi == (mp | (1u << (i - 1))) ? 1 : 0);
         }
         if (!use[i]) continue;
         const size_t before = g->tables.size();
         WeightTable *t = nullptr;
-        // a row-prefix table (8 B per CSR entry) makes single-backward draws a search;
-        // past the budget the sampler scans the anchor row instead
-        const bool rowp = i > 0 && p->nback[i] == 1 && (size_t)g->nnz * sizeof(uint64_t) <= g->rowp_budget;
+        // a row-prefix table makes single-backward draws a search; when the full table
+        // (8 B per CSR entry) is past the budget only the highest-degree rows get one
+        // and the sampler scans the other anchor rows
+        const bool rowp = i > 0 && p->nback[i] == 1;
         rc = build_weight_table(g, p->cfg[i], i == 0, rowp, &t);
         if (rc != AGIS_OK) return rc;
         built |= g->tables.size() != before;
@@ -191,8 +193,9 @@ int make_dev_query(agis_graph *g, const agis_pattern *p, const agis_opts *o, Dev
         if (i == 0) {
             s.pref = t->pref;
             dq->W1 = t->total;
-        } else if (p->nback[i] == 1 && rowp) {
+        } else if (rowp && t->rowp) {
             s.pref = t->rowp;
+            s.rp_mode = t->rowp_partial ? 2 : 1;
         }
     }
     if (!use[0]) dq->W1 = (uint64_t)g->nnz;
@@ -541,6 +544,8 @@ void graph_release(agis_graph *g)
         cudaFree(g->hits);
         cudaFree(g->hub_id);
         cudaFree(g->hub_bits);
+        cudaFree(g->rp_base);
+        cudaFree(g->rp_rows);
     }
     delete g;
     ctx_release(c);

@@ -442,6 +442,27 @@ __device__ TrialOut run_trial(const GraphView &g, const DevQuery &Q, uint64_t t,
         uint64_t W = 0, qv = 0;
         int32_t v = -1;
         STEP_T0
+        // a single-backward step searches its anchor row's prefix when it has one
+        // (always under f_uniform, whose prefix is the position)
+        bool direct = false;
+        const uint64_t *Prow = nullptr;
+        if (i > 0 && S.nb == 1) {
+            if (!S.approx) {
+                direct = true;
+            } else if (S.pref) {
+                const int32_t a = tau_s[S.back[0]];
+                if (S.rp_mode == 1) {
+                    Prow = S.pref + __ldg(g.off + a);
+                    direct = true;
+                } else {
+                    const int64_t b = __ldg(g.rp_base + a);
+                    if (b >= 0) {
+                        Prow = S.pref + b;
+                        direct = true;
+                    }
+                }
+            }
+        }
         if (i == 0) {
             // ---- step 1: the whole vertex set
             W = Q.W1;
@@ -453,7 +474,7 @@ __device__ TrialOut run_trial(const GraphView &g, const DevQuery &Q, uint64_t t,
             qv = S.approx ? __ldg(S.q + v) : (uint64_t)(__ldg(g.off + v + 1) - __ldg(g.off + v));
             cur = -1;
             STEP_T1(0)
-        } else if (S.nb == 1 && (S.pref != nullptr || !S.approx)) {
+        } else if (direct) {
             // ---- one backward neighbour: S = N(a) \ tau
             const int jb = S.back[0];
             const int32_t a = tau_s[jb];
@@ -476,7 +497,7 @@ __device__ TrialOut run_trial(const GraphView &g, const DevQuery &Q, uint64_t t,
             }
             const uint32_t xmask = __ballot_sync(kFull, member);
             const uint64_t excl = warp_sum_u64(xq);
-            const uint64_t *P = S.approx ? S.pref + a_start : nullptr;
+            const uint64_t *P = S.approx ? Prow : nullptr;
             const uint64_t total = d <= 0 ? 0 : (S.approx ? __ldg(P + d - 1) : (uint64_t)d);
             W = total - excl;
             if (W == 0) { out.sectors = sec; return out; }
@@ -638,7 +659,7 @@ __device__ TrialOut run_trial(const GraphView &g, const DevQuery &Q, uint64_t t,
                 }
             }
         }
-        if (i > 0 && !(S.nb == 1 && (S.pref != nullptr || !S.approx))) { STEP_T1(4) }
+        if (i > 0 && !direct) { STEP_T1(4) }
         X = X * ((double)W / (double)qv);
         __syncwarp();
         if (lane == 0) tau_s[i] = v;
@@ -795,7 +816,7 @@ int launch_sampler(agis_graph *g, LaunchBuffers &lb, int grid, const DumpView *d
                    cudaStream_t stream, uint64_t implicit_first, uint64_t implicit_count,
                    uint64_t *tile_out)
 {
-    GraphView gv{g->off, g->cols, g->nv, g->nnz, g->hub_id, g->hub_bits, g->hub_words};
+    GraphView gv{g->off, g->cols, g->nv, g->nnz, g->hub_id, g->hub_bits, g->hub_words, g->rp_base};
     const WorkItem *items = implicit_count ? nullptr : lb.d_items;
     uint64_t *out = tile_out ? tile_out : lb.d_out;
     if (dump) {
@@ -827,7 +848,7 @@ int add_sampler_node(agis_graph *g, LaunchBuffers &lb, int grid, cudaGraph_t gra
     static uint64_t z0, z1;
     static char *scr;
     static uint32_t cap;
-    gv = GraphView{g->off, g->cols, g->nv, g->nnz, g->hub_id, g->hub_bits, g->hub_words};
+    gv = GraphView{g->off, g->cols, g->nv, g->nnz, g->hub_id, g->hub_bits, g->hub_words, g->rp_base};
     none = DumpView{nullptr, nullptr, nullptr, nullptr, 0};
     q = lb.d_queries;
     it = lb.d_items;

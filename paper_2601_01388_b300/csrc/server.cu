@@ -56,12 +56,14 @@ size_t extra_bytes(agis_graph *g, const agis_pattern &p, const agis_opts &o)
     uint8_t use[kMaxK];
     agis_pattern_decide(&p, o.mode, o.beta, use);
     std::map<uint64_t, std::pair<bool, bool>> need;   // cfg -> (vertex prefix, row prefix)
-    const bool rowp_ok = (size_t)g->nnz * sizeof(uint64_t) <= g->rowp_budget;
+    // a row prefix of every row, or of the highest-degree rows within the budget
+    const size_t rowp_bytes = rowp_full_fits(g) ? sizeof(uint64_t) * (size_t)g->nnz
+                                                 : std::min<size_t>(g->rowp_budget, sizeof(uint64_t) * (size_t)g->nnz);
     for (int i = 0; i < p.k; ++i) {
         if (!use[i]) continue;
         auto &f = need[cfg_key(p.cfg[i])];
         f.first = f.first || i == 0;
-        f.second = f.second || (i > 0 && p.nback[i] == 1 && rowp_ok);
+        f.second = f.second || (i > 0 && p.nback[i] == 1);
     }
     size_t extra = 0;
     for (const auto &kv : need) {
@@ -69,7 +71,7 @@ size_t extra_bytes(agis_graph *g, const agis_pattern &p, const agis_opts &o)
         const bool have = it != g->tables.end();
         if (!have) extra += sizeof(uint64_t) * (size_t)g->nv;
         if (kv.second.first && !(have && it->second.pref)) extra += sizeof(uint64_t) * (size_t)g->nv;
-        if (kv.second.second && !(have && it->second.rowp)) extra += sizeof(uint64_t) * (size_t)g->nnz;
+        if (kv.second.second && !(have && it->second.rowp)) extra += rowp_bytes;
     }
     return extra;
 }

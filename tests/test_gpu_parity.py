@@ -265,3 +265,33 @@ def test_scale14_estimates_cover_exact_counts(agis, oracle_mod, rmat14, name, mo
     part = agis.estimate(g, agis.Pattern(k, edges), agis.default_opts(mode=mode, seed=1, eps=0.0, max_trials=8192))
     assert part["hits"] == s["hits"] and part["sectors"] == s["sectors"]
     assert part["sum_x"] == pytest.approx(s["sum_x"], rel=REL, abs=0)
+
+
+# ------------------------------------------------------------------ every sampler path
+
+def _policies(nnz):
+    return {
+        "bitmaps_for_degree_4_and_up": dict(bitmap_min_degree=4),
+        "lists_of_64_entries": dict(list_entries=64),
+        "no_row_prefix": dict(row_prefix_bytes=8),
+        "row_prefix_of_top_rows": dict(row_prefix_bytes=8 * nnz // 3),
+        "all_together": dict(bitmap_min_degree=16, list_entries=128, row_prefix_bytes=8 * nnz // 5),
+    }
+
+
+@pytest.mark.parametrize("policy", ["bitmaps_for_degree_4_and_up", "lists_of_64_entries", "no_row_prefix",
+                                    "row_prefix_of_top_rows", "all_together"])
+def test_trials_bit_exact_under_memory_policies(agis, ctx, oracle_mod, policy):
+    """The memory policy picks among bitmap probes, merges and searches, listed and
+    list-free intersections, full, partial or no row prefixes; none of it may
+    change a trial."""
+    off, cols = I.rmat_graph(12, 16, seed=3)
+    nsum, hits = oracle_mod.graph_stats(off, cols, 1)
+    g = agis.Graph(ctx, off, cols)
+    g.set_memory_policy(**_policies(len(cols))[policy])
+    g.preprocess(1, CMIN)
+    for name in ["4-clique", "5-clique", "house", "5-cycle", "triangle", "4-path", "chordal-5-cycle",
+                 "tailed-triangle", "4-star"]:
+        for mode in MODES:
+            compare_dumps(agis, oracle_mod, off, cols, g, nsum, hits, name, mode, 777, 1500)
+    g.close()
