@@ -397,14 +397,14 @@ def batch64(agis, ctx, scale, stream):
 def large_graph(agis, ctx, scale):
     """R-MAT scale 28 with edge factor 32 built on the device (int64 offsets, int32
     columns); time to +-1% at 95% confidence for the 6-clique and the 7-cycle under
-    f_approx (D^pi) and f_uniform, at most 2^30 trials each.  Row prefixes are kept
-    to the highest-degree rows within 24 GB per configuration."""
+    f_approx (D^pi) (at most 2^30 trials) and f_uniform (at most 2^28).  Row
+    prefixes are kept to the highest-degree rows within 12 GB per configuration."""
     import torch
     from paper_2601_01388_b300 import inputs as I
     t0 = time.perf_counter()
     g = agis.Graph.rmat(ctx, scale, 32, 0.57, 0.19, 0.19, seed=1)
     t_gen = time.perf_counter() - t0
-    g.set_memory_policy(row_prefix_bytes=24 << 30)
+    g.set_memory_policy(row_prefix_bytes=12 << 30)
     t0 = time.perf_counter()
     g.preprocess(1, CMIN)
     t_prep = time.perf_counter() - t0
@@ -413,9 +413,10 @@ def large_graph(agis, ctx, scale):
                     f"max degree {info['max_degree']}", "generate_s": t_gen, "preprocess_s": t_prep, "runs": []}
     for name in ("6-clique", "7-cycle"):
         p = agis.Pattern(*I.PATTERNS[name])
-        for mode, label in ((0, "f_approx (D^pi)"), (2, "f_uniform")):
+        for mode, label, cap in ((0, "f_approx (D^pi)", 1 << 30), (2, "f_uniform", 1 << 28)):
+            g.drop_tables()
             o = agis.default_opts(mode=mode, seed=7, eps=0.01, delta=0.05, chunk_trials=1 << 16,
-                                  min_trials=1 << 16, max_trials=1 << 30)
+                                  min_trials=1 << 16, max_trials=cap)
             t1 = time.perf_counter()
             agis.prepare(g, p, o)
             t_tab = time.perf_counter() - t1

@@ -294,6 +294,96 @@ __device__ __forceinline__ void emit_window(bool ok, int32_t x, uint64_t w, int3
 #endif
 constexpr int kGroups = AGIS_FILTER_GROUPS;
 
+// A bitmap probe fetches a 32-byte sector per list entry, a merge reads the other
+// row once at 4 bytes per entry; the merge is used while m < AGIS_MERGE_RATIO * n.
+#ifndef AGIS_MERGE_RATIO
+#define AGIS_MERGE_RATIO 0
+#endif
+
+// Running weights of out[0, cnt): gathers q for two windows at a time.
+__device__ __forceinline__ uint64_t weigh_list(const int32_t *out, uint32_t cnt, uint64_t *out_pw,
+                                               const uint64_t *q, bool approx, int lane)
+{
+    uint64_t carry = 0;
+    for (uint32_t b = 0; b < cnt; b += 64) {
+        int32_t x[2];
+        uint64_t w[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const uint32_t idx = b + 32 * u + lane;
+            x[u] = idx < cnt ? out[idx] : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) w[u] = (b + 32 * u + lane < cnt) ? (approx ? __ldg(q + x[u]) : 1u) : 0u;
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const uint64_t incl = warp_incl_scan(w[u], lane);
+            const uint32_t idx = b + 32 * u + lane;
+            if (idx < cnt) out_pw[idx] = carry + incl;
+            carry += __shfl_sync(kFull, incl, 31);
+        }
+    }
+    return carry;
+}
+
+// Per-lane merge: lane l takes the l-th of 32 equal segments of L, finds where the
+// segment starts in R by a binary search, and merges its segment against R
+// sequentially (each lane walks its own cache lines, so R is read once and the
+// loads hit L1); survivors go to the lane's own stretch of tmp (at the segment's
+// offset, so at most n entries), then are compacted in order into out.
+template <bool kWeigh>
+__device__ uint32_t filter_lane_merge(const int32_t *L, uint32_t n, const int32_t *R, int64_t m,
+                                      const int32_t *tau_s, int tau_n, int32_t *out, int32_t *tmp,
+                                      uint64_t *out_pw, uint32_t cap, const uint64_t *q, bool approx,
+                                      uint64_t *W, int lane)
+{
+    const uint32_t seg = (n + 31) >> 5;
+    const uint32_t l0 = min(n, (uint32_t)lane * seg), l1 = min(n, l0 + seg);
+    uint32_t c = 0;
+    if (l0 < l1 && m > 0) {
+        const int32_t first = __ldg(L + l0);
+        int64_t lo = 0, len = m;                  // first j with R[j] >= first
+        while (len > 0) {
+            const int64_t half = len >> 1;
+            if (__ldg(R + lo + half) < first) { lo += half + 1; len -= half + 1; } else len = half;
+        }
+        int64_t j = lo;
+        uint32_t i = l0;
+        if (j < m) {
+            int32_t x = first, y = __ldg(R + j);
+            for (;;) {
+                if (x < y) {
+                    if (++i >= l1) break;
+                    x = __ldg(L + i);
+                } else if (x > y) {
+                    if (++j >= m) break;
+                    y = __ldg(R + j);
+                } else {
+                    bool ok = true;
+                    for (int t = 0; t < tau_n; ++t) ok = ok && (x != tau_s[t]);
+                    if (ok) tmp[l0 + c++] = x;
+                    if (++i >= l1 || ++j >= m) break;
+                    x = __ldg(L + i);
+                    y = __ldg(R + j);
+                }
+            }
+        }
+    }
+    uint32_t incl = c;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += t;
+    }
+    const uint32_t total = __shfl_sync(kFull, incl, 31);
+    if (total > cap) return total;
+    __syncwarp();
+    const uint32_t base = incl - c;
+    for (uint32_t k = 0; k < c; ++k) out[base + k] = tmp[l0 + k];
+    __syncwarp();
+    if (kWeigh) *W = weigh_list(out, total, out_pw, q, approx, lane);
+    return total;
+}
+
 template <bool kWeigh>
 __device__ uint32_t filter_list(const int32_t *L, uint32_t n, const int32_t *R, int64_t m,
                                 const uint32_t *Rbits, const int32_t *tau_s, int tau_n, int32_t *out,
@@ -302,6 +392,11 @@ __device__ uint32_t filter_list(const int32_t *L, uint32_t n, const int32_t *R, 
 {
     uint32_t cnt = 0;
     uint64_t carry = 0;
+    // tmp: the id staging of the per-lane merge lives in the (not yet written)
+    // running-weight array of out's list, room for 2 * cap ids
+    if (R && n >= 256 && m >= 256 && n <= 2 * cap && (!Rbits || m < (int64_t)AGIS_MERGE_RATIO * n))
+        return filter_lane_merge<kWeigh>(L, n, R, m, tau_s, tau_n, out, reinterpret_cast<int32_t *>(out_pw),
+                                         out_pw, cap, q, approx, W, lane);
     if (Rbits || !R) {
         // Survivor ids first: 16-byte loads of four consecutive entries per lane,
         // kGroups groups of 128 entries per iteration, so 4 * kGroups bitmap probes
@@ -567,7 +662,7 @@ __device__ TrialOut run_trial(const GraphView &g, const DevQuery &Q, uint64_t t,
                                               ws.pw[nxt], ws.cap, S.q, S.approx != 0, &Wl, lane);
                     } else {
                         n = filter_list<false>(src, n, R, m, Rb, tau_s, pss == 0 ? tau_n : 0, ws.xs[nxt],
-                                               nullptr, ws.cap, S.q, S.approx != 0, nullptr, lane);
+                                               ws.pw[nxt], ws.cap, S.q, S.approx != 0, nullptr, lane);
                         src = ws.xs[nxt];
                         nxt = 1 - nxt;
                     }
