@@ -67,6 +67,9 @@ def parse_args():
     ap.add_argument("--serve", action="store_true",
                     help="also run the serving load (saturation, then Poisson at 50/80/95%%)")
     ap.add_argument("--serve-seconds", type=float, default=15.0)
+    ap.add_argument("--ablation", action="store_true",
+                    help="also run the f_approx term ablation and the beta sweep on the bench graph "
+                         "(time and trials to +-1%%)")
     return ap.parse_args()
 
 
@@ -432,6 +435,57 @@ def large_graph(agis, ctx, scale):
     return out
 
 
+# ------------------------------------------------------------------ ablation and beta
+
+ABLATION_PATTERNS = ["4-clique", "4-path", "5-cycle", "house", "5-clique"]
+# certainty below 1 on some steps (Def. decision_function), so beta changes the plan
+BETA_PATTERNS = {
+    "4-cycle": None, "5-cycle": None, "house": None, "7-cycle": None,
+    "rand6-a": (6, [(0, 2), (0, 3), (0, 5), (1, 3), (1, 5), (2, 3), (2, 5), (3, 4), (4, 5)]),
+    "rand7-b": (7, [(0, 2), (0, 3), (0, 5), (0, 6), (1, 3), (1, 5), (1, 6), (2, 4), (3, 5), (3, 6),
+                    (4, 6)]),
+}
+BETAS = [("-inf", 1, 0.0), ("0.5", 0, 0.5), ("0.7", 0, 0.7), ("0.8", 0, 0.8), ("0.9", 0, 0.9),
+         ("1.0", 0, 1.0), ("+inf", 2, 0.0)]
+
+
+def ablation(agis, g, cap_log2=28):
+    """Sec. 6.3 and Sec. 6.2 on the resident graph: trials and seconds to +-1% (95%)
+    with the incremental versions of f_approx (T[F1]; + T[I1]; + T[F2]) and f_uniform,
+    then across beta (-inf = f_approx on every step, +inf = f_uniform on every step).
+    Runs stop at 2^cap_log2 trials; an unconverged run reports the trials it would
+    need, trials * (eps_hat / eps)^2, since the half-width shrinks as 1/sqrt(n)."""
+    from paper_2601_01388_b300 import inputs as I
+    acc = dict(eps=0.01, delta=0.05, chunk_trials=1 << 16, min_trials=1 << 16, max_trials=1 << cap_log2)
+
+    def run(p, o):
+        g.drop_tables()
+        t0 = time.perf_counter()
+        agis.prepare(g, p, o)
+        t_tab = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        r = agis.estimate(g, p, o)
+        dt = time.perf_counter() - t0
+        need = r["trials"] if r["converged"] else int(r["trials"] * (r["eps_hat"] / 0.01) ** 2)
+        return {"trials": r["trials"], "converged": r["converged"], "trials_needed": need,
+                "estimate": r["estimate"], "eps_hat": r["eps_hat"], "tables_s": t_tab, "s": dt}
+
+    out = {"cap_trials": 1 << cap_log2, "terms": [], "beta": []}
+    for name in ABLATION_PATTERNS:
+        p = agis.Pattern(*I.PATTERNS[name])
+        for terms, label in ((1, "T[F1]"), (3, "T[F1]+T[I1]"), (7, "T[F1]+T[I1]+T[F2]"), (0, "f_uniform")):
+            o = agis.default_opts(mode=2 if terms == 0 else 1, terms=terms, seed=31, **acc)
+            out["terms"].append({"pattern": name, "f": label, **run(p, o)})
+    for name, pat in BETA_PATTERNS.items():
+        k, edges = pat if pat is not None else I.PATTERNS[name]
+        p = agis.Pattern(k, edges)
+        for label, mode, beta in BETAS:
+            o = agis.default_opts(mode=mode, beta=beta, seed=37, **acc)
+            uses = [int(u) for u in p.decide(mode, beta)]
+            out["beta"].append({"pattern": name, "beta": label, "use_approx": uses, **run(p, o)})
+    return out
+
+
 # ------------------------------------------------------------------ GPU arm
 
 def run_gpu(args, world, rank, local):
@@ -630,6 +684,10 @@ def run_gpu(args, world, rank, local):
         if args.serve:
             serving = serve_load(agis, g, args.serve_seconds)
 
+        abl = None
+        if args.ablation:
+            abl = ablation(agis, g)
+
     cpu = None
     if pool is not None:
         t_prep = pool.preprocess()
@@ -671,6 +729,8 @@ def run_gpu(args, world, rank, local):
         line["batch64"] = batching
     if large is not None:
         line["large_graph"] = large
+    if abl is not None:
+        line["ablation"] = abl
     return line
 
 

@@ -423,14 +423,25 @@ static uint64_t step_weight(const orc_query *Q, int i, int32_t v)
     return orc_quantise(w, d, p->nback[i], p->f1[i], Q->shift[i]);
 }
 
-orc_query *orc_query_create(int64_t nv, const int64_t *off, const int32_t *cols,
-                            const uint64_t *nsum, const uint32_t *hits, double c_min,
-                            int32_t k, int32_t ne, const int32_t *edges,
-                            int32_t mode, double beta, uint64_t seed)
+/* terms: which factors of Eq. probability_function are kept (bit 0 T[F1], bit 1
+ * T[I1], bit 2 T[F2]; 0 = all three), the incremental versions of the Sec. 6.3
+ * ablation.  A dropped factor is 1, i.e. its exponent in the step configuration is
+ * zero (for T[F1]: binom(d-|B|, 0), which keeps d >= |B|). */
+orc_query *orc_query_create_terms(int64_t nv, const int64_t *off, const int32_t *cols,
+                                  const uint64_t *nsum, const uint32_t *hits, double c_min,
+                                  int32_t k, int32_t ne, const int32_t *edges,
+                                  int32_t mode, double beta, uint64_t seed, int32_t terms)
 {
     orc_query *Q = (orc_query *)calloc(1, sizeof(orc_query));
     if (!Q) return NULL;
     if (orc_plan_compile(k, ne, edges, &Q->plan) != 0) { free(Q); return NULL; }
+    if (terms != 0) {
+        for (int i = 0; i < Q->plan.k; ++i) {
+            if (!(terms & 1)) Q->plan.f1[i] = 0;
+            if (!(terms & 2)) Q->plan.ieff[i] = 0;
+            if (!(terms & 4)) Q->plan.f2[i] = 0;
+        }
+    }
     Q->nv = nv; Q->nnz = off[nv]; Q->off = off; Q->cols = cols; Q->nsum = nsum; Q->hits = hits;
     Q->c_min = c_min; Q->seed = seed;
     orc_plan_decide(&Q->plan, mode, beta, Q->use_approx);
@@ -456,6 +467,14 @@ orc_query *orc_query_create(int64_t nv, const int64_t *off, const int32_t *cols,
     }
     Q->W1 = run;
     return Q;
+}
+
+orc_query *orc_query_create(int64_t nv, const int64_t *off, const int32_t *cols,
+                            const uint64_t *nsum, const uint32_t *hits, double c_min,
+                            int32_t k, int32_t ne, const int32_t *edges,
+                            int32_t mode, double beta, uint64_t seed)
+{
+    return orc_query_create_terms(nv, off, cols, nsum, hits, c_min, k, ne, edges, mode, beta, seed, 0);
 }
 
 void orc_query_free(orc_query *Q)
@@ -726,6 +745,30 @@ static uint64_t bf_rec(int64_t nv, const int64_t *off, const int32_t *cols, int 
         total += bf_rec(nv, off, cols, k, adj, map, depth + 1);
     }
     return total;
+}
+
+/* n_(v) of Sec. 4.1 for every v: embeddings whose first pattern vertex in the
+ * matching order pi maps to v (so that f_ideal(v | ()) = n_(v) / C(G,P), Thm. 1). */
+int orc_bruteforce_by_first(int64_t nv, const int64_t *off, const int32_t *cols,
+                            int32_t k, int32_t ne, const int32_t *edges, int64_t *counts)
+{
+    orc_plan plan;
+    if (orc_plan_compile(k, ne, edges, &plan) != 0) return -1;
+    /* relabel the pattern so that pattern vertex 0 is u_1 = pi(1) */
+    int inv[ORC_MAXK];
+    for (int i = 0; i < k; ++i) inv[plan.order[i]] = i;
+    unsigned adj[ORC_MAXK] = {0};
+    for (int e = 0; e < ne; ++e) {
+        int a = inv[edges[2 * e]], b = inv[edges[2 * e + 1]];
+        adj[a] |= 1u << b;
+        adj[b] |= 1u << a;
+    }
+    int32_t map[ORC_MAXK];
+    for (int64_t v = 0; v < nv; ++v) {
+        map[0] = (int32_t)v;
+        counts[v] = (int64_t)bf_rec(nv, off, cols, k, adj, map, 1);
+    }
+    return 0;
 }
 
 int64_t orc_bruteforce_count(int64_t nv, const int64_t *off, const int32_t *cols,

@@ -78,6 +78,11 @@ def lib():
                                        C.c_double, C.c_int32, C.c_int32, P(C.c_int32),
                                        C.c_int32, C.c_double, C.c_uint64]
         L.orc_query_create.restype = C.c_void_p
+        L.orc_query_create_terms.argtypes = L.orc_query_create.argtypes + [C.c_int32]
+        L.orc_query_create_terms.restype = C.c_void_p
+        L.orc_bruteforce_by_first.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32,
+                                              P(C.c_int32), C.c_void_p]
+        L.orc_bruteforce_by_first.restype = C.c_int
         L.orc_query_free.argtypes = [C.c_void_p]
         L.orc_query_info.argtypes = [C.c_void_p, P(Plan), P(C.c_int32), P(C.c_int32),
                                      P(C.c_uint64)]
@@ -202,6 +207,17 @@ def z_of_delta(delta):
     return float(lib().orc_z_of_delta(delta))
 
 
+def bruteforce_by_first(off, cols, k, edges):
+    """n_(v) for every vertex v: embeddings whose first matched pattern vertex is v."""
+    off = np.ascontiguousarray(off, dtype=np.int64)
+    cols = np.ascontiguousarray(cols, dtype=np.int32)
+    flat, p = _edges_arr(edges)
+    out = np.zeros(len(off) - 1, dtype=np.int64)
+    if lib().orc_bruteforce_by_first(len(off) - 1, _ptr(off), _ptr(cols), k, len(flat) // 2, p, _ptr(out)) != 0:
+        raise ValueError("invalid pattern")
+    return out
+
+
 def bruteforce_count(off, cols, k, edges):
     off = np.ascontiguousarray(off, dtype=np.int64)
     cols = np.ascontiguousarray(cols, dtype=np.int32)
@@ -221,7 +237,7 @@ class Query:
     """One pattern query on one graph: keeps the oracle's per-query state."""
 
     def __init__(self, off, cols, k, edges, *, nsum=None, hits=None, graph_seed=1,
-                 c_min=2.0 ** -10, mode=MODE_AUTO, beta=0.8, seed=1):
+                 c_min=2.0 ** -10, mode=MODE_AUTO, beta=0.8, seed=1, terms=0):
         self.off = np.ascontiguousarray(off, dtype=np.int64)
         self.cols = np.ascontiguousarray(cols, dtype=np.int32)
         if nsum is None or hits is None:
@@ -230,9 +246,9 @@ class Query:
         self.hits = np.ascontiguousarray(hits, dtype=np.uint32)
         self._flat, p = _edges_arr(edges)
         self.k = k
-        self._h = lib().orc_query_create(len(self.off) - 1, _ptr(self.off), _ptr(self.cols),
-                                         _ptr(self.nsum), _ptr(self.hits), c_min, k,
-                                         len(self._flat) // 2, p, mode, beta, seed)
+        self._h = lib().orc_query_create_terms(len(self.off) - 1, _ptr(self.off), _ptr(self.cols),
+                                               _ptr(self.nsum), _ptr(self.hits), c_min, k,
+                                               len(self._flat) // 2, p, mode, beta, seed, terms)
         if not self._h:
             raise ValueError("invalid pattern or out of memory")
 

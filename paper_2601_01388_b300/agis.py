@@ -39,7 +39,7 @@ EXPORTS = [
 
 class Opts(C.Structure):
     _fields_ = [("eps", C.c_double), ("delta", C.c_double), ("beta", C.c_double),
-                ("mode", C.c_int32), ("reserved", C.c_int32), ("seed", C.c_uint64),
+                ("mode", C.c_int32), ("terms", C.c_int32), ("seed", C.c_uint64),
                 ("min_trials", C.c_uint64), ("max_trials", C.c_uint64),
                 ("chunk_trials", C.c_uint64)]
 
@@ -126,7 +126,10 @@ def _ptr(a):
 def default_opts(**kw):
     o = Opts()
     _lib.agis_default_opts(C.byref(o))
+    names = {f[0] for f in Opts._fields_}
     for k, v in kw.items():
+        if k not in names:
+            raise TypeError(f"unknown option {k!r}")
         setattr(o, k, v)
     return o
 

@@ -194,6 +194,8 @@ int sampler_occupancy(int *blocks_per_sm);
 // runtime.cu
 int make_dev_query(agis_graph *g, const agis_pattern *p, const agis_opts *o, DevQuery *dq,
                    double *t_prep);
+// step configuration of step i with the factors that `terms` drops set to exponent 0
+void effective_cfg(const agis_pattern *p, int i, int32_t terms, int32_t out[4]);
 int ensure_buffers(LaunchBuffers &lb, size_t n_queries, size_t n_items);
 int grid_for(agis_graph *g, size_t n_items);
 int ensure_scratch(agis_graph *g, LaunchBuffers &lb, int grid);

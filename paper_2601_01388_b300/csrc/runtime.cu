@@ -83,6 +83,7 @@ int check_opts(const agis_opts *o)
 {
     if (!o) return AGIS_ERR_ARG;
     if (o->mode < 0 || o->mode > 2) return AGIS_ERR_ARG;
+    if (o->terms < 0 || o->terms > 7) return AGIS_ERR_ARG;
     if (o->chunk_trials == 0 || o->chunk_trials % kTile != 0) return AGIS_ERR_ARG;
     if (o->max_trials == 0) return AGIS_ERR_ARG;
     if (o->eps > 0.0 && !(o->delta > 0.0 && o->delta < 1.0)) return AGIS_ERR_ARG;
@@ -155,6 +156,14 @@ int ensure_scratch(agis_graph *g, LaunchBuffers &lb, int grid)
     return AGIS_OK;
 }
 
+void effective_cfg(const agis_pattern *p, int i, int32_t terms, int32_t out[4])
+{
+    out[0] = p->cfg[i][0];
+    out[1] = (terms == 0 || (terms & 1)) ? p->cfg[i][1] : 0;
+    out[2] = (terms == 0 || (terms & 2)) ? p->cfg[i][2] : 0;
+    out[3] = (terms == 0 || (terms & 4)) ? p->cfg[i][3] : 0;
+}
+
 int make_dev_query(agis_graph *g, const agis_pattern *p, const agis_opts *o, DevQuery *dq,
                    double *t_prep)
 {
@@ -186,7 +195,9 @@ int make_dev_query(agis_graph *g, const agis_pattern *p, const agis_opts *o, Dev
         // (8 B per CSR entry) is past the budget only the highest-degree rows get one
         // and the sampler scans the other anchor rows
         const bool rowp = i > 0 && p->nback[i] == 1;
-        rc = build_weight_table(g, p->cfg[i], i == 0, rowp, &t);
+        int32_t cfg[4];
+        effective_cfg(p, i, o->terms, cfg);
+        rc = build_weight_table(g, cfg, i == 0, rowp, &t);
         if (rc != AGIS_OK) return rc;
         built |= g->tables.size() != before;
         s.q = t->q;

@@ -61,7 +61,9 @@ size_t extra_bytes(agis_graph *g, const agis_pattern &p, const agis_opts &o)
                                                  : std::min<size_t>(g->rowp_budget, sizeof(uint64_t) * (size_t)g->nnz);
     for (int i = 0; i < p.k; ++i) {
         if (!use[i]) continue;
-        auto &f = need[cfg_key(p.cfg[i])];
+        int32_t cfg[4];
+        effective_cfg(&p, i, o.terms, cfg);
+        auto &f = need[cfg_key(cfg)];
         f.first = f.first || i == 0;
         f.second = f.second || (i > 0 && p.nback[i] == 1);
     }
@@ -147,7 +149,9 @@ void scheduler(agis_server *s)
                 agis_pattern_decide(&q->pat, q->opts.mode, q->opts.beta, use);
                 for (int i = 0; i < q->pat.k; ++i) {
                     if (!use[i]) continue;
-                    const uint64_t key = cfg_key(q->pat.cfg[i]);
+                    int32_t cfg[4];
+                    effective_cfg(&q->pat, i, q->opts.terms, cfg);
+                    const uint64_t key = cfg_key(cfg);
                     if (std::find(q->pinned.begin(), q->pinned.end(), key) != q->pinned.end()) continue;
                     g->tables[key].pins++;
                     q->pinned.push_back(key);
