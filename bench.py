@@ -67,6 +67,12 @@ def parse_args():
     ap.add_argument("--serve", action="store_true",
                     help="also run the serving load (saturation, then Poisson at 50/80/95%%)")
     ap.add_argument("--serve-seconds", type=float, default=15.0)
+    ap.add_argument("--concentration", action="store_true",
+                    help="also run the concentration workload: all 6 four-vertex and 21 five-vertex "
+                         "connected patterns as one batch each, to +-1%%")
+    ap.add_argument("--dag", action="store_true",
+                    help="also run the 4/5/6-clique queries on the degree-ordered orientation vs the "
+                         "undirected graph (time to +-1%%)")
     ap.add_argument("--ablation", action="store_true",
                     help="also run the f_approx term ablation and the beta sweep on the bench graph "
                          "(time and trials to +-1%%)")
@@ -450,7 +456,7 @@ BETAS = [("-inf", 1, 0.0), ("0.5", 0, 0.5), ("0.7", 0, 0.7), ("0.8", 0, 0.8), ("
 
 
 def ablation(agis, g, cap_log2=28):
-    """Sec. 6.3 and Sec. 6.2 on the resident graph: trials and seconds to +-1% (95%)
+    """Sec. 6.2 and Sec. 6.1 on the resident graph: trials and seconds to +-1% (95%)
     with the incremental versions of f_approx (T[F1]; + T[I1]; + T[F2]) and f_uniform,
     then across beta (-inf = f_approx on every step, +inf = f_uniform on every step).
     Runs stop at 2^cap_log2 trials; an unconverged run reports the trials it would
@@ -483,6 +489,72 @@ def ablation(agis, g, cap_log2=28):
             o = agis.default_opts(mode=mode, beta=beta, seed=37, **acc)
             uses = [int(u) for u in p.decide(mode, beta)]
             out["beta"].append({"pattern": name, "beta": label, "use_approx": uses, **run(p, o)})
+    return out
+
+
+# ------------------------------------------------------------------ concentration
+
+def concentration_run(agis, g, cap_log2=30):
+    """Sec. 6.3 on the resident graph: every connected 4-vertex (6) and 5-vertex (21)
+    pattern as one batch, each to +-1% (95%); concentrations of the non-induced
+    subgraph counts, and the variation distance between two independently seeded
+    batches as an empirical accuracy figure."""
+    from paper_2601_01388_b300 import concentration as K
+    out = {}
+    for k in (4, 5):
+        pats = K.connected_patterns(k)
+        ps = [agis.Pattern(*p) for p in pats]
+        vecs = []
+        for rep in range(2):
+            opts = [agis.default_opts(eps=0.01, delta=0.05, seed=1000 * (rep + 1) + i, chunk_trials=1 << 16,
+                                      min_trials=1 << 16, max_trials=1 << cap_log2) for i in range(len(ps))]
+            g.drop_tables()
+            t0 = time.perf_counter()
+            rs = agis.estimate_batch(g, ps, opts)
+            dt = time.perf_counter() - t0
+            c = K.concentration(K.subgraph_counts([r["estimate"] for r in rs], k))
+            vecs.append(c)
+            if rep == 0:
+                out[f"k{k}"] = {"patterns": len(ps), "s": dt, "trials": int(sum(r["trials"] for r in rs)),
+                                "all_converged": all(r["converged"] for r in rs),
+                                "concentration": [float(x) for x in c],
+                                "edges": [p[1] for p in pats]}
+        out[f"k{k}"]["variation_distance_between_seeds"] = K.variation_distance(vecs[0], vecs[1])
+    return out
+
+
+# ------------------------------------------------------------------ orientation for cliques
+
+def cliques_oriented(agis, g, cap_log2=32):
+    """Sec. 5.4's orientation for clique patterns on the resident graph: time to
+    orient and preprocess the DAG, then time and trials to +-1% (95%) for the 4-, 5-
+    and 6-clique on the undirected graph and on the orientation (same seeds)."""
+    from paper_2601_01388_b300 import inputs as I
+    t0 = time.perf_counter()
+    o = g.orient()
+    t_orient = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    o.preprocess(1, CMIN)
+    t_prep = time.perf_counter() - t0
+    info = o.info()
+    out = {"orient_s": t_orient, "preprocess_s": t_prep, "nnz": info["nnz"], "max_out_degree": info["max_degree"],
+           "runs": []}
+    for name in ("4-clique", "5-clique", "6-clique"):
+        p = agis.Pattern(*I.PATTERNS[name])
+        for label, graph in (("undirected", g), ("oriented", o)):
+            opts = agis.default_opts(mode=0, seed=53, eps=0.01, delta=0.05, chunk_trials=1 << 16,
+                                     min_trials=1 << 16, max_trials=1 << cap_log2)
+            graph.drop_tables()
+            t0 = time.perf_counter()
+            agis.prepare(graph, p, opts)
+            t_tab = time.perf_counter() - t0
+            t0 = time.perf_counter()
+            r = agis.estimate(graph, p, opts)
+            dt = time.perf_counter() - t0
+            out["runs"].append({"pattern": name, "graph": label, "tables_s": t_tab, "s": dt, "trials": r["trials"],
+                                "converged": r["converged"], "estimate": r["estimate"], "eps_hat": r["eps_hat"],
+                                "samples_per_s": r["trials"] / dt if dt > 0 else None})
+    o.close()
     return out
 
 
@@ -688,6 +760,14 @@ def run_gpu(args, world, rank, local):
         if args.ablation:
             abl = ablation(agis, g)
 
+        conc = None
+        if args.concentration:
+            conc = concentration_run(agis, g)
+
+        dag = None
+        if args.dag:
+            dag = cliques_oriented(agis, g)
+
     cpu = None
     if pool is not None:
         t_prep = pool.preprocess()
@@ -731,6 +811,10 @@ def run_gpu(args, world, rank, local):
         line["large_graph"] = large
     if abl is not None:
         line["ablation"] = abl
+    if conc is not None:
+        line["concentration"] = conc
+    if dag is not None:
+        line["cliques_oriented"] = dag
     return line
 
 

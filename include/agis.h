@@ -71,7 +71,7 @@ typedef struct {
     int32_t mode;           /* agis_mode                                               */
     int32_t terms;          /* factors of Eq. probability_function kept: bit 0 T[F1],
                                bit 1 T[I1], bit 2 T[F2]; 0 = all (the method). Others
-                               give the incremental versions of the Sec. 6.3 ablation */
+                               give the incremental versions of the Sec. 6.2 ablation */
     uint64_t seed;          /* Philox key of this query's trials                       */
     uint64_t min_trials;    /* Alg. 1 is not consulted before this many trials         */
     uint64_t max_trials;    /* hard budget; with eps <= 0 exactly this many run        */
@@ -146,12 +146,32 @@ int agis_graph_weight_table(agis_graph *g, const int32_t cfg[4], uint64_t *q,
 int agis_graph_row_prefix(agis_graph *g, const int32_t cfg[4], uint64_t *row_prefix);
 
 /* agis_graph_validate: re-checks the CSR conventions above on the device (e.g. for a
- * generated graph).  Returns OK or GRAPH. */
+ * generated graph); on an oriented graph (agis_graph_orient) the reverse of every
+ * entry must be absent instead of present.  Returns OK or GRAPH. */
 int agis_graph_validate(agis_graph *g);
 
 /* agis_graph_copy_csr: copies the device CSR to caller-owned host arrays off[nv+1]
  * (int64) and cols[nnz] (int32); either may be NULL. */
 int agis_graph_copy_csr(const agis_graph *g, int64_t *off, int32_t *cols);
+
+/* agis_graph_orient: the degree-ordered orientation that Sec. 5.4 applies to clique
+ * patterns (the graph turned into a DAG by dropping every edge that points from a
+ * higher- to a lower-degree vertex).  Row u of *out keeps v when (d(u), u) < (d(v), v)
+ * lexicographically, degrees taken in g, in g's ascending order; so each k-clique is
+ * exactly one chain v1 -> ... -> vk with every later vertex in the out-rows of all
+ * earlier ones, and a row holds at most about sqrt(2|E|) entries.  *out is a new
+ * device graph with half of g's entries and g's memory policy; it needs
+ * agis_graph_preprocess (the Sec. 4.4 statistics over out-rows) and agis_graph_free,
+ * and g stays valid.  Queries on it take clique patterns only (others: PATTERN); their
+ * f_approx weight uses |B| = 0 in T[F1] (no earlier vertex is in a later one's
+ * out-row), and results report estimate = cliques * k! (embeddings, as on g) and
+ * subgraphs = cliques, with mean/var/sum_x the per-trial moments (cliques).
+ * Errors: ARG, STATE (g is itself oriented), NOMEM, CUDA. */
+int agis_graph_orient(agis_graph *g, agis_graph **out);
+
+/* agis_graph_is_oriented: 1 for a graph made by agis_graph_orient, 0 for a loaded
+ * or generated one, ARG for NULL. */
+int agis_graph_is_oriented(const agis_graph *g);
 
 /* agis_graph_set_memory_policy: device-memory budgets of the optional structures
  * that speed up sampling (0 keeps a setting): row_prefix_bytes -- the largest

@@ -406,6 +406,7 @@ typedef struct {
     uint64_t seed;
     orc_plan plan;
     int32_t use_approx[ORC_MAXK];
+    int32_t wb[ORC_MAXK];  /* |B| in the weight's T[F1]: nback, or 0 on an orientation */
     int32_t shift[ORC_MAXK];
     uint64_t *cum1;       /* step-1 f_approx: inclusive running weight over v = 0..nv-1 */
     uint64_t W1;
@@ -418,23 +419,30 @@ static uint64_t step_weight(const orc_query *Q, int i, int32_t v)
     int64_t d = Q->off[v + 1] - Q->off[v];
     if (!Q->use_approx[i]) return i == 0 ? (uint64_t)d : 1u;   /* f_uniform (Sec. 5.3) */
     const orc_plan *p = &Q->plan;
-    double w = orc_weight(d, Q->nsum[v], Q->hits[v], Q->c_min, p->nback[i], p->f1[i],
+    double w = orc_weight(d, Q->nsum[v], Q->hits[v], Q->c_min, Q->wb[i], p->f1[i],
                           p->ieff[i], p->f2[i]);
-    return orc_quantise(w, d, p->nback[i], p->f1[i], Q->shift[i]);
+    return orc_quantise(w, d, Q->wb[i], p->f1[i], Q->shift[i]);
 }
 
 /* terms: which factors of Eq. probability_function are kept (bit 0 T[F1], bit 1
- * T[I1], bit 2 T[F2]; 0 = all three), the incremental versions of the Sec. 6.3
+ * T[I1], bit 2 T[F2]; 0 = all three), the incremental versions of the Sec. 6.2
  * ablation.  A dropped factor is 1, i.e. its exponent in the step configuration is
  * zero (for T[F1]: binom(d-|B|, 0), which keeps d >= |B|). */
-orc_query *orc_query_create_terms(int64_t nv, const int64_t *off, const int32_t *cols,
-                                  const uint64_t *nsum, const uint32_t *hits, double c_min,
-                                  int32_t k, int32_t ne, const int32_t *edges,
-                                  int32_t mode, double beta, uint64_t seed, int32_t terms)
+/* oriented: the CSR is a degree-ordered orientation (orc_orient) and the pattern a
+ * clique.  Each clique is then one trajectory, every step intersects the out-rows
+ * of all earlier vertices, and the weight takes |B| = 0 since no earlier vertex
+ * lies in a later vertex's out-row (Sec. 5.4 orientation for cliques). */
+orc_query *orc_query_create_ex(int64_t nv, const int64_t *off, const int32_t *cols,
+                               const uint64_t *nsum, const uint32_t *hits, double c_min,
+                               int32_t k, int32_t ne, const int32_t *edges,
+                               int32_t mode, double beta, uint64_t seed, int32_t terms,
+                               int32_t oriented)
 {
     orc_query *Q = (orc_query *)calloc(1, sizeof(orc_query));
     if (!Q) return NULL;
     if (orc_plan_compile(k, ne, edges, &Q->plan) != 0) { free(Q); return NULL; }
+    if (oriented && ne != k * (k - 1) / 2) { free(Q); return NULL; }
+    for (int i = 0; i < Q->plan.k; ++i) Q->wb[i] = oriented ? 0 : Q->plan.nback[i];
     if (terms != 0) {
         for (int i = 0; i < Q->plan.k; ++i) {
             if (!(terms & 1)) Q->plan.f1[i] = 0;
@@ -448,7 +456,7 @@ orc_query *orc_query_create_terms(int64_t nv, const int64_t *off, const int32_t 
     const orc_plan *p = &Q->plan;
     for (int i = 0; i < p->k; ++i)
         Q->shift[i] = Q->use_approx[i]
-            ? orc_quant_shift(nv, off, nsum, hits, c_min, p->nback[i], p->f1[i], p->ieff[i], p->f2[i])
+            ? orc_quant_shift(nv, off, nsum, hits, c_min, Q->wb[i], p->f1[i], p->ieff[i], p->f2[i])
             : 0;
     int64_t maxd = 1;
     for (int64_t v = 0; v < nv; ++v) if (off[v + 1] - off[v] > maxd) maxd = off[v + 1] - off[v];
@@ -469,12 +477,39 @@ orc_query *orc_query_create_terms(int64_t nv, const int64_t *off, const int32_t 
     return Q;
 }
 
+orc_query *orc_query_create_terms(int64_t nv, const int64_t *off, const int32_t *cols,
+                                  const uint64_t *nsum, const uint32_t *hits, double c_min,
+                                  int32_t k, int32_t ne, const int32_t *edges,
+                                  int32_t mode, double beta, uint64_t seed, int32_t terms)
+{
+    return orc_query_create_ex(nv, off, cols, nsum, hits, c_min, k, ne, edges, mode, beta, seed, terms, 0);
+}
+
 orc_query *orc_query_create(int64_t nv, const int64_t *off, const int32_t *cols,
                             const uint64_t *nsum, const uint32_t *hits, double c_min,
                             int32_t k, int32_t ne, const int32_t *edges,
                             int32_t mode, double beta, uint64_t seed)
 {
-    return orc_query_create_terms(nv, off, cols, nsum, hits, c_min, k, ne, edges, mode, beta, seed, 0);
+    return orc_query_create_ex(nv, off, cols, nsum, hits, c_min, k, ne, edges, mode, beta, seed, 0, 0);
+}
+
+/* The degree-ordered orientation of Sec. 5.4: u -> v is kept when d(u) < d(v), or
+ * d(u) = d(v) and u < v.  off_out has nv + 1 entries and cols_out room for off[nv]
+ * entries; rows keep their ascending order.  Returns the number of kept entries. */
+int64_t orc_orient(int64_t nv, const int64_t *off, const int32_t *cols, int64_t *off_out, int32_t *cols_out)
+{
+    int64_t n = 0;
+    off_out[0] = 0;
+    for (int64_t u = 0; u < nv; ++u) {
+        const int64_t du = off[u + 1] - off[u];
+        for (int64_t j = off[u]; j < off[u + 1]; ++j) {
+            const int32_t v = cols[j];
+            const int64_t dv = off[v + 1] - off[v];
+            if (du < dv || (du == dv && u < v)) cols_out[n++] = v;
+        }
+        off_out[u + 1] = n;
+    }
+    return n;
 }
 
 void orc_query_free(orc_query *Q)

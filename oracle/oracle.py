@@ -80,6 +80,10 @@ def lib():
         L.orc_query_create.restype = C.c_void_p
         L.orc_query_create_terms.argtypes = L.orc_query_create.argtypes + [C.c_int32]
         L.orc_query_create_terms.restype = C.c_void_p
+        L.orc_query_create_ex.argtypes = L.orc_query_create.argtypes + [C.c_int32, C.c_int32]
+        L.orc_query_create_ex.restype = C.c_void_p
+        L.orc_orient.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+        L.orc_orient.restype = C.c_int64
         L.orc_bruteforce_by_first.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32,
                                               P(C.c_int32), C.c_void_p]
         L.orc_bruteforce_by_first.restype = C.c_int
@@ -207,6 +211,16 @@ def z_of_delta(delta):
     return float(lib().orc_z_of_delta(delta))
 
 
+def orient(off, cols):
+    """Degree-ordered orientation (Sec. 5.4): (off, cols) of the out-rows."""
+    off = np.ascontiguousarray(off, dtype=np.int64)
+    cols = np.ascontiguousarray(cols, dtype=np.int32)
+    oo = np.zeros(len(off), dtype=np.int64)
+    oc = np.zeros(max(len(cols), 1), dtype=np.int32)
+    n = lib().orc_orient(len(off) - 1, _ptr(off), _ptr(cols), _ptr(oo), _ptr(oc))
+    return oo, oc[:n].copy()
+
+
 def bruteforce_by_first(off, cols, k, edges):
     """n_(v) for every vertex v: embeddings whose first matched pattern vertex is v."""
     off = np.ascontiguousarray(off, dtype=np.int64)
@@ -237,7 +251,7 @@ class Query:
     """One pattern query on one graph: keeps the oracle's per-query state."""
 
     def __init__(self, off, cols, k, edges, *, nsum=None, hits=None, graph_seed=1,
-                 c_min=2.0 ** -10, mode=MODE_AUTO, beta=0.8, seed=1, terms=0):
+                 c_min=2.0 ** -10, mode=MODE_AUTO, beta=0.8, seed=1, terms=0, oriented=False):
         self.off = np.ascontiguousarray(off, dtype=np.int64)
         self.cols = np.ascontiguousarray(cols, dtype=np.int32)
         if nsum is None or hits is None:
@@ -246,9 +260,9 @@ class Query:
         self.hits = np.ascontiguousarray(hits, dtype=np.uint32)
         self._flat, p = _edges_arr(edges)
         self.k = k
-        self._h = lib().orc_query_create_terms(len(self.off) - 1, _ptr(self.off), _ptr(self.cols),
-                                               _ptr(self.nsum), _ptr(self.hits), c_min, k,
-                                               len(self._flat) // 2, p, mode, beta, seed, terms)
+        self._h = lib().orc_query_create_ex(len(self.off) - 1, _ptr(self.off), _ptr(self.cols),
+                                            _ptr(self.nsum), _ptr(self.hits), c_min, k,
+                                            len(self._flat) // 2, p, mode, beta, seed, terms, int(oriented))
         if not self._h:
             raise ValueError("invalid pattern or out of memory")
 

@@ -29,7 +29,7 @@ TILE = 1024
 EXPORTS = [
     "agis_status_str", "agis_default_opts", "agis_create", "agis_destroy", "agis_graph_load_csr",
     "agis_graph_preprocess", "agis_graph_info", "agis_graph_stats_copy", "agis_graph_weight_table",
-    "agis_graph_row_prefix", "agis_graph_set_memory_policy", "agis_graph_validate", "agis_graph_copy_csr", "agis_graph_drop_tables", "agis_graph_free", "agis_graph_generate_rmat", "agis_graph_generate_chunglu",
+    "agis_graph_row_prefix", "agis_graph_orient", "agis_graph_is_oriented", "agis_graph_set_memory_policy", "agis_graph_validate", "agis_graph_copy_csr", "agis_graph_drop_tables", "agis_graph_free", "agis_graph_generate_rmat", "agis_graph_generate_chunglu",
     "agis_pattern_create", "agis_pattern_info", "agis_pattern_decide", "agis_pattern_free",
     "agis_estimate", "agis_estimate_batch", "agis_autotune", "agis_dump_trials", "agis_sample_device",
     "agis_prepare", "agis_z_of_delta", "agis_kernel_launches", "agis_prefix_sum_u64_noalloc", "agis_probe_random_read", "agis_step_timers", "agis_server_create", "agis_server_submit", "agis_server_poll",
@@ -70,6 +70,8 @@ _sig = {
     "agis_graph_row_prefix": ([VP, P(C.c_int32), VP], C.c_int),
     "agis_graph_set_memory_policy": ([VP, C.c_uint64, C.c_uint64, C.c_int64, C.c_uint32], C.c_int),
     "agis_graph_validate": ([VP], C.c_int),
+    "agis_graph_orient": ([VP, P(VP)], C.c_int),
+    "agis_graph_is_oriented": ([VP], C.c_int),
     "agis_graph_copy_csr": ([VP, VP, VP], C.c_int),
     "agis_graph_drop_tables": ([VP], C.c_int),
     "agis_graph_free": ([VP], C.c_int),
@@ -273,6 +275,19 @@ class Graph:
                "agis_graph_generate_chunglu")
         self.h = h
         return self
+
+    def orient(self):
+        """The degree-ordered orientation for clique patterns (a new Graph)."""
+        o = Graph.__new__(Graph)
+        o.ctx = self.ctx
+        h = VP()
+        _check(_lib.agis_graph_orient(self.h, C.byref(h)), "agis_graph_orient")
+        o.h = h
+        return o
+
+    @property
+    def oriented(self):
+        return _lib.agis_graph_is_oriented(self.h) == 1
 
     def preprocess(self, seed=1, c_min=2.0 ** -10):
         _check(_lib.agis_graph_preprocess(self.h, seed, c_min), "agis_graph_preprocess")

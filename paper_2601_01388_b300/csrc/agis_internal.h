@@ -147,6 +147,7 @@ struct agis_graph {
     uint64_t *nsum = nullptr;
     uint32_t *hits = nullptr;
     bool prepped = false;
+    bool oriented = false;      // degree-ordered orientation (agis_graph_orient): out-rows only
     double c_min = 0.0;
     uint64_t prep_seed = 0;
     std::map<uint64_t, agis::WeightTable> tables;
@@ -194,8 +195,9 @@ int sampler_occupancy(int *blocks_per_sm);
 // runtime.cu
 int make_dev_query(agis_graph *g, const agis_pattern *p, const agis_opts *o, DevQuery *dq,
                    double *t_prep);
-// step configuration of step i with the factors that `terms` drops set to exponent 0
-void effective_cfg(const agis_pattern *p, int i, int32_t terms, int32_t out[4]);
+// weight configuration of step i: the factors that `terms` drops get exponent 0, and
+// on an oriented graph |B| is 0 (no backward vertex lies in a later vertex's out-row)
+void effective_cfg(const agis_pattern *p, int i, int32_t terms, bool oriented, int32_t out[4]);
 int ensure_buffers(LaunchBuffers &lb, size_t n_queries, size_t n_items);
 int grid_for(agis_graph *g, size_t n_items);
 int ensure_scratch(agis_graph *g, LaunchBuffers &lb, int grid);
@@ -217,6 +219,7 @@ struct QueryRun {
     double ck_sx = 0.0, ck_sx2 = 0.0;
     bool finished = false;
     bool converged = false;
+    bool oriented = false;        // sampled on a degree-ordered orientation: X counts cliques once
     int launches = 0;
     double t_prep = 0.0;
 };

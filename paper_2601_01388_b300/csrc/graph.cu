@@ -41,8 +41,9 @@ __global__ void k_check_offsets(const int64_t *off, int64_t nv, int64_t nnz, int
     }
 }
 
-// one warp per row: range, self-loop, strict order and presence of the reverse entry
-__global__ void k_check_rows(const int64_t *off, const int32_t *cols, int64_t nv, int *err)
+// one warp per row: range, self-loop, strict order, and the reverse entry present
+// (undirected graph) or absent (oriented graph)
+__global__ void k_check_rows(const int64_t *off, const int32_t *cols, int64_t nv, int oriented, int *err)
 {
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -52,7 +53,7 @@ __global__ void k_check_rows(const int64_t *off, const int32_t *cols, int64_t nv
         for (int64_t i = s + lane; i < e; i += 32) {
             const int32_t x = cols[i];
             bool bad = x < 0 || x >= nv || x == v || (i > s && cols[i - 1] >= x);
-            if (!bad) bad = row_find(cols + off[x], off[x + 1] - off[x], (int32_t)v) < 0;
+            if (!bad) bad = (row_find(cols + off[x], off[x + 1] - off[x], (int32_t)v) < 0) != (oriented != 0);
             if (bad) atomicOr(err, 2);
         }
     }
@@ -306,6 +307,57 @@ __global__ void k_row_prefix_partial(const int64_t *off, const int32_t *cols, co
             }
             if (i < e) dst[i - s] = carry + w;
             carry += __shfl_sync(kFull, w, 31);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- degree ordering
+
+// u -> v is kept when (d(u), u) < (d(v), v) lexicographically
+__device__ __forceinline__ bool orient_keep(int64_t du, int64_t u, int64_t dv, int64_t v)
+{
+    return du < dv || (du == dv && u < v);
+}
+
+// kept[u] = out-degree of u in the orientation; one warp per row
+__global__ void k_orient_count(const int64_t *off, const int32_t *cols, int64_t nv, uint64_t *kept)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t u = warp; u < nv; u += nwarps) {
+        const int64_t s = off[u], e = off[u + 1], du = e - s;
+        uint32_t n = 0;
+        for (int64_t i = s + lane; i < e; i += 32) {
+            const int32_t v = __ldg(cols + i);
+            n += orient_keep(du, u, __ldg(off + v + 1) - __ldg(off + v), v);
+        }
+        for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(kFull, n, o);
+        if (lane == 0) kept[u] = n;
+    }
+}
+
+// writes the kept entries of each row, in row order, from out_off[u]; one warp per row
+__global__ void k_orient_fill(const int64_t *off, const int32_t *cols, int64_t nv, const int64_t *out_off,
+                              int32_t *out_cols)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t u = warp; u < nv; u += nwarps) {
+        const int64_t s = off[u], e = off[u + 1], du = e - s;
+        int64_t pos = out_off[u];
+        for (int64_t i0 = s; i0 < e; i0 += 32) {
+            const int64_t i = i0 + lane;
+            int32_t v = 0;
+            bool keep = false;
+            if (i < e) {
+                v = __ldg(cols + i);
+                keep = orient_keep(du, u, __ldg(off + v + 1) - __ldg(off + v), v);
+            }
+            const unsigned b = __ballot_sync(kFull, keep);
+            if (keep) out_cols[pos + __popc(b & ((1u << lane) - 1u))] = v;
+            pos += __popc(b);
         }
     }
 }
@@ -604,7 +656,7 @@ extern "C" int agis_graph_load_csr(agis_ctx *ctx, const void *offsets, int offse
     if (err) { cudaFree(d_err); return fail(AGIS_ERR_GRAPH); }
     if (validate) {
         count_launch();
-        k_check_rows<<<grid_stride_blocks(g, nv * 32, 256), 256, 0, st>>>(g->off, g->cols, nv, d_err);
+        k_check_rows<<<grid_stride_blocks(g, nv * 32, 256), 256, 0, st>>>(g->off, g->cols, nv, 0, d_err);
         cudaMemcpyAsync(&err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
         if (cudaStreamSynchronize(st) != cudaSuccess) { cudaFree(d_err); return fail(AGIS_ERR_CUDA); }
         if (err) { cudaFree(d_err); return fail(AGIS_ERR_GRAPH); }
@@ -742,7 +794,8 @@ extern "C" int agis_graph_validate(agis_graph *g)
     cudaError_t e = cudaStreamSynchronize(st);
     if (e == cudaSuccess && !err) {
         count_launch();
-        k_check_rows<<<grid_stride_blocks(g, g->nv * 32, 256), 256, 0, st>>>(g->off, g->cols, g->nv, d_err);
+        k_check_rows<<<grid_stride_blocks(g, g->nv * 32, 256), 256, 0, st>>>(g->off, g->cols, g->nv,
+                                                                             g->oriented ? 1 : 0, d_err);
         cudaMemcpyAsync(&err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
         e = cudaStreamSynchronize(st);
     }
@@ -760,6 +813,67 @@ extern "C" int agis_graph_copy_csr(const agis_graph *g, int64_t *off, int32_t *c
     if (cols && g->nnz > 0)
         AGIS_CUDA_TRY(cudaMemcpy(cols, g->cols, sizeof(int32_t) * (size_t)g->nnz, cudaMemcpyDeviceToHost));
     return AGIS_OK;
+}
+
+extern "C" int agis_graph_orient(agis_graph *g, agis_graph **out)
+{
+    if (!g || !out) return AGIS_ERR_ARG;
+    *out = nullptr;
+    if (g->oriented) return AGIS_ERR_STATE;
+    std::lock_guard<std::recursive_mutex> lk(g->mu);
+    AGIS_CUDA_TRY(cudaSetDevice(g->ctx->device));
+    cudaStream_t st = g->ctx->stream;
+    agis_graph *o = new (std::nothrow) agis_graph();
+    if (!o) return AGIS_ERR_NOMEM;
+    o->ctx = g->ctx;
+    o->nv = g->nv;
+    o->oriented = true;
+    o->rowp_budget = g->rowp_budget;
+    o->bitmap_budget = g->bitmap_budget;
+    o->bitmap_min_degree = g->bitmap_min_degree;
+    o->list_cap = g->list_cap;
+    uint64_t *kept = nullptr;
+    auto fail = [&](int rc) {
+        cudaStreamSynchronize(st);
+        cudaFree(kept);
+        cudaFree(o->off);
+        cudaFree(o->cols);
+        delete o;
+        return rc;
+    };
+    if (cudaMalloc(&o->off, sizeof(int64_t) * (size_t)(g->nv + 1)) != cudaSuccess ||
+        cudaMalloc(&kept, sizeof(uint64_t) * (size_t)g->nv) != cudaSuccess)
+        return fail(AGIS_ERR_NOMEM);
+    const int blocks = grid_stride_blocks(g, g->nv * 32, 256);
+    count_launch();
+    k_orient_count<<<blocks, 256, 0, st>>>(g->off, g->cols, g->nv, kept);
+    if (cudaMemsetAsync(o->off, 0, sizeof(int64_t), st) != cudaSuccess) return fail(AGIS_ERR_CUDA);
+    // offsets: off[0] = 0 and off[u + 1] = the inclusive running sum of the kept counts
+    int rc = inclusive_scan_u64(g->ctx, kept, g->nv, (uint64_t *)(o->off + 1));
+    if (rc != AGIS_OK) return fail(rc);
+    std::vector<int64_t> h((size_t)g->nv + 1);
+    if (cudaMemcpyAsync(h.data(), o->off, sizeof(int64_t) * (size_t)(g->nv + 1), cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return fail(AGIS_ERR_CUDA);
+    o->nnz = h[(size_t)g->nv];
+    for (int64_t v = 0; v < g->nv; ++v) o->max_deg = std::max(o->max_deg, h[(size_t)v + 1] - h[(size_t)v]);
+    // 16 entries of padding for the sampler's 16-byte row loads, zeroed
+    if (cudaMalloc(&o->cols, sizeof(int32_t) * (size_t)(o->nnz + 16)) != cudaSuccess) return fail(AGIS_ERR_NOMEM);
+    if (cudaMemsetAsync(o->cols + o->nnz, 0, sizeof(int32_t) * 16, st) != cudaSuccess) return fail(AGIS_ERR_CUDA);
+    count_launch();
+    k_orient_fill<<<blocks, 256, 0, st>>>(g->off, g->cols, g->nv, o->off, o->cols);
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) return fail(AGIS_ERR_CUDA);
+    cudaFree(kept);
+    ctx_retain(o->ctx);
+    *out = o;
+    return AGIS_OK;
+}
+
+extern "C" int agis_graph_is_oriented(const agis_graph *g)
+{
+    if (!g) return AGIS_ERR_ARG;
+    return g->oriented ? 1 : 0;
 }
 
 // ---------------------------------------------------------------- prefix sum without allocation

@@ -156,9 +156,9 @@ int ensure_scratch(agis_graph *g, LaunchBuffers &lb, int grid)
     return AGIS_OK;
 }
 
-void effective_cfg(const agis_pattern *p, int i, int32_t terms, int32_t out[4])
+void effective_cfg(const agis_pattern *p, int i, int32_t terms, bool oriented, int32_t out[4])
 {
-    out[0] = p->cfg[i][0];
+    out[0] = oriented ? 0 : p->cfg[i][0];
     out[1] = (terms == 0 || (terms & 1)) ? p->cfg[i][1] : 0;
     out[2] = (terms == 0 || (terms & 2)) ? p->cfg[i][2] : 0;
     out[3] = (terms == 0 || (terms & 4)) ? p->cfg[i][3] : 0;
@@ -168,6 +168,9 @@ int make_dev_query(agis_graph *g, const agis_pattern *p, const agis_opts *o, Dev
                    double *t_prep)
 {
     if (!g->prepped) return AGIS_ERR_STATE;
+    if (g->oriented)
+        for (int i = 0; i < p->k; ++i)
+            if (p->nback[i] != i) return AGIS_ERR_PATTERN;   // an orientation serves cliques only
     uint8_t use[kMaxK];
     int rc = agis_pattern_decide(p, o->mode, o->beta, use);
     if (rc != AGIS_OK) return rc;
@@ -196,7 +199,7 @@ int make_dev_query(agis_graph *g, const agis_pattern *p, const agis_opts *o, Dev
         // and the sampler scans the other anchor rows
         const bool rowp = i > 0 && p->nback[i] == 1;
         int32_t cfg[4];
-        effective_cfg(p, i, o->terms, cfg);
+        effective_cfg(p, i, o->terms, g->oriented, cfg);
         rc = build_weight_table(g, cfg, i == 0, rowp, &t);
         if (rc != AGIS_OK) return rc;
         built |= g->tables.size() != before;
@@ -225,6 +228,7 @@ int init_run(agis_graph *g, const agis_pattern *p, const agis_opts *o, QueryRun 
     r.z = o->eps > 0.0 ? agis_z_of_delta(o->delta) : 0.0;
     r.max_tiles = (o->max_trials + kTile - 1) / kTile;
     r.tiles_per_chunk = o->chunk_trials / kTile;
+    r.oriented = g->oriented;
     return make_dev_query(g, p, o, &r.dq, &r.t_prep);
 }
 
@@ -298,8 +302,11 @@ void fill_result(const QueryRun &r, agis_result *out)
     const double n = (double)r.ck_trials;
     double mu = 0, var = 0, eh = INFINITY;
     if (r.ck_trials > 0) alg1(n, r.ck_sx, r.ck_sx2, r.z > 0 ? r.z : agis_z_of_delta(r.o.delta > 0 && r.o.delta < 1 ? r.o.delta : 0.05), &mu, &var, &eh);
-    out->estimate = mu;
-    out->subgraphs = r.p && r.p->aut ? mu / (double)r.p->aut : 0.0;
+    // on an orientation every clique is one trajectory, so mu estimates the cliques
+    // themselves and the embedding count is mu * |Aut| = mu * k!
+    const double aut = r.p && r.p->aut ? (double)r.p->aut : 0.0;
+    out->estimate = r.oriented ? mu * aut : mu;
+    out->subgraphs = r.oriented ? mu : (aut > 0 ? mu / aut : 0.0);
     out->mean = mu;
     out->var = var;
     out->eps_hat = eh;

@@ -62,7 +62,7 @@ size_t extra_bytes(agis_graph *g, const agis_pattern &p, const agis_opts &o)
     for (int i = 0; i < p.k; ++i) {
         if (!use[i]) continue;
         int32_t cfg[4];
-        effective_cfg(&p, i, o.terms, cfg);
+        effective_cfg(&p, i, o.terms, g->oriented, cfg);
         auto &f = need[cfg_key(cfg)];
         f.first = f.first || i == 0;
         f.second = f.second || (i > 0 && p.nback[i] == 1);
@@ -150,7 +150,7 @@ void scheduler(agis_server *s)
                 for (int i = 0; i < q->pat.k; ++i) {
                     if (!use[i]) continue;
                     int32_t cfg[4];
-                    effective_cfg(&q->pat, i, q->opts.terms, cfg);
+                    effective_cfg(&q->pat, i, q->opts.terms, g->oriented, cfg);
                     const uint64_t key = cfg_key(cfg);
                     if (std::find(q->pinned.begin(), q->pinned.end(), key) != q->pinned.end()) continue;
                     g->tables[key].pins++;

@@ -1,8 +1,8 @@
-"""The incremental versions of f_approx (Sec. 6.3: T[F1] only, + T[I1], + T[F2]) and
-the decision threshold beta (Sec. 6.2).  CPU: the oracle with factors dropped is
+"""The incremental versions of f_approx (Sec. 6.2: T[F1] only, + T[I1], + T[F2]) and
+the decision threshold beta (Sec. 6.1).  CPU: the oracle with factors dropped is
 still unbiased (Thm. 2 needs only positive probabilities on every embedding), is
 exact where the dropped factors are constant, and n_(v) of Sec. 4.1 is pinned by
-closed forms; the step-1 KL divergences to f_ideal behave as Sec. 6.3 reports.
+closed forms; the step-1 KL divergences to f_ideal behave as Sec. 6.2 reports.
 GPU: sampling with any term mask and any beta is bit-identical to the oracle."""
 import math
 
@@ -96,7 +96,7 @@ def test_triangle_first_term_only_closed_form(oracle_mod):
         assert x[t] == pytest.approx(want, rel=1e-12)
 
 
-# ---------------------------------------------------------------- Sec. 6.3, step-1 KL
+# ---------------------------------------------------------------- Sec. 6.2, step-1 KL
 
 def step1_kl(oracle_mod, off, cols, nsum, hits, name, terms):
     """KL(f_ideal(. | ()) || f) for the step-1 distribution f of the given mask
