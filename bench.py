@@ -70,6 +70,9 @@ def parse_args():
     ap.add_argument("--concentration", action="store_true",
                     help="also run the concentration workload: all 6 four-vertex and 21 five-vertex "
                          "connected patterns as one batch each, to +-1%%")
+    ap.add_argument("--anchor", action="store_true",
+                    help="also compare the anchor draw with the S_tau build (time to +-1%%) on the bench patterns "
+                         "and the 6-clique")
     ap.add_argument("--dag", action="store_true",
                     help="also run the 4/5/6-clique queries on the degree-ordered orientation vs the "
                          "undirected graph (time to +-1%%)")
@@ -558,6 +561,33 @@ def cliques_oriented(agis, g, cap_log2=32):
     return out
 
 
+# ------------------------------------------------------------------ anchor draw
+
+def anchor_vs_exact(agis, g, names, cap_log2=32):
+    """Time and trials to +-1% (95%) for each pattern with S_tau built as in Alg. 3
+    and with the anchor draw (proposal from the shortest backward row, closing edges
+    checked afterwards), same seeds."""
+    from paper_2601_01388_b300 import inputs as I
+    out = []
+    for name in names:
+        p = agis.Pattern(*I.PATTERNS[name])
+        for anchor in (0, 1):
+            o = agis.default_opts(mode=0, seed=61, anchor=anchor, eps=0.01, delta=0.05, chunk_trials=1 << 16,
+                                  min_trials=1 << 16, max_trials=1 << cap_log2)
+            g.drop_tables()
+            t0 = time.perf_counter()
+            agis.prepare(g, p, o)
+            t_tab = time.perf_counter() - t0
+            t0 = time.perf_counter()
+            r = agis.estimate(g, p, o)
+            dt = time.perf_counter() - t0
+            out.append({"pattern": name, "draw": "anchor" if anchor else "S_tau", "tables_s": t_tab, "s": dt,
+                        "trials": r["trials"], "hit_rate": r["hits"] / max(r["trials"], 1),
+                        "converged": r["converged"], "estimate": r["estimate"],
+                        "samples_per_s": r["trials"] / dt if dt > 0 else None})
+    return out
+
+
 # ------------------------------------------------------------------ GPU arm
 
 def run_gpu(args, world, rank, local):
@@ -768,6 +798,10 @@ def run_gpu(args, world, rank, local):
         if args.dag:
             dag = cliques_oriented(agis, g)
 
+        anch = None
+        if args.anchor:
+            anch = anchor_vs_exact(agis, g, names + ["6-clique"])
+
     cpu = None
     if pool is not None:
         t_prep = pool.preprocess()
@@ -815,6 +849,8 @@ def run_gpu(args, world, rank, local):
         line["concentration"] = conc
     if dag is not None:
         line["cliques_oriented"] = dag
+    if anch is not None:
+        line["anchor_draw"] = anch
     return line
 
 

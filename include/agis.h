@@ -76,6 +76,12 @@ typedef struct {
     uint64_t min_trials;    /* Alg. 1 is not consulted before this many trials         */
     uint64_t max_trials;    /* hard budget; with eps <= 0 exactly this many run        */
     uint64_t chunk_trials;  /* checkpoint spacing for Alg. 1; multiple of 1024         */
+    int32_t anchor;         /* 1: a step with several backward vertices draws from the
+                               shortest backward row (minus tau) with the step's weights
+                               and the trial fails unless the drawn vertex closes every
+                               other backward edge, instead of building S_tau (Alg. 3);
+                               still unbiased by Thm. 2.  0 (default): S_tau as in Alg. 3 */
+    int32_t reserved;       /* must be 0                                               */
 } agis_opts;
 
 typedef struct {

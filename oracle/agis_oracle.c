@@ -407,6 +407,7 @@ typedef struct {
     orc_plan plan;
     int32_t use_approx[ORC_MAXK];
     int32_t wb[ORC_MAXK];  /* |B| in the weight's T[F1]: nback, or 0 on an orientation */
+    int32_t anchor;        /* steps with several backward vertices use the anchor draw */
     int32_t shift[ORC_MAXK];
     uint64_t *cum1;       /* step-1 f_approx: inclusive running weight over v = 0..nv-1 */
     uint64_t W1;
@@ -436,10 +437,11 @@ orc_query *orc_query_create_ex(int64_t nv, const int64_t *off, const int32_t *co
                                const uint64_t *nsum, const uint32_t *hits, double c_min,
                                int32_t k, int32_t ne, const int32_t *edges,
                                int32_t mode, double beta, uint64_t seed, int32_t terms,
-                               int32_t oriented)
+                               int32_t oriented, int32_t anchor)
 {
     orc_query *Q = (orc_query *)calloc(1, sizeof(orc_query));
     if (!Q) return NULL;
+    Q->anchor = anchor != 0;
     if (orc_plan_compile(k, ne, edges, &Q->plan) != 0) { free(Q); return NULL; }
     if (oriented && ne != k * (k - 1) / 2) { free(Q); return NULL; }
     for (int i = 0; i < Q->plan.k; ++i) Q->wb[i] = oriented ? 0 : Q->plan.nback[i];
@@ -482,7 +484,7 @@ orc_query *orc_query_create_terms(int64_t nv, const int64_t *off, const int32_t 
                                   int32_t k, int32_t ne, const int32_t *edges,
                                   int32_t mode, double beta, uint64_t seed, int32_t terms)
 {
-    return orc_query_create_ex(nv, off, cols, nsum, hits, c_min, k, ne, edges, mode, beta, seed, terms, 0);
+    return orc_query_create_ex(nv, off, cols, nsum, hits, c_min, k, ne, edges, mode, beta, seed, terms, 0, 0);
 }
 
 orc_query *orc_query_create(int64_t nv, const int64_t *off, const int32_t *cols,
@@ -490,7 +492,7 @@ orc_query *orc_query_create(int64_t nv, const int64_t *off, const int32_t *cols,
                             int32_t k, int32_t ne, const int32_t *edges,
                             int32_t mode, double beta, uint64_t seed)
 {
-    return orc_query_create_ex(nv, off, cols, nsum, hits, c_min, k, ne, edges, mode, beta, seed, 0, 0);
+    return orc_query_create_ex(nv, off, cols, nsum, hits, c_min, k, ne, edges, mode, beta, seed, 0, 0, 0);
 }
 
 /* The degree-ordered orientation of Sec. 5.4: u -> v is kept when d(u) < d(v), or
@@ -566,6 +568,69 @@ static int64_t build_candidates(const orc_query *Q, int i, const int32_t *tau, u
     return n;
 }
 
+/* Anchor draw, the alternative to building S_tau for a step with several backward
+ * vertices: the proposal set is the row of one backward vertex, the anchor (the
+ * shortest backward row, the first in backward order on ties), minus tau, with the
+ * step's weights (q under f_approx, 1 under f_uniform).  The drawn vertex must then
+ * be a neighbour of every other backward vertex (the closing edges), else the trial
+ * returns 0.  Every extension in S_tau keeps a positive probability q / W, so Thm. 2
+ * still gives an unbiased estimate; S_tau is never built.  Returns the anchor's
+ * index in the backward list and fills cand/candq; *W is the proposal total. */
+static int anchor_candidates(const orc_query *Q, int i, const int32_t *tau, uint64_t *W, int64_t *n_out)
+{
+    const orc_plan *p = &Q->plan;
+    int a = 0;
+    int64_t da = -1;
+    for (int b = 0; b < p->nback[i]; ++b) {
+        int32_t u = tau[p->back[i][b]];
+        int64_t d = Q->off[u + 1] - Q->off[u];
+        if (da < 0 || d < da) { da = d; a = b; }
+    }
+    int32_t anchor = tau[p->back[i][a]];
+    int64_t n = 0;
+    uint64_t sum = 0;
+    for (int64_t e = Q->off[anchor]; e < Q->off[anchor + 1]; ++e) {
+        int32_t x = Q->cols[e];
+        int in_tau = 0;
+        for (int j = 0; j < i; ++j) if (tau[j] == x) { in_tau = 1; break; }
+        if (in_tau) continue;
+        uint64_t q = step_weight(Q, i, x);
+        Q->cand[n] = x;
+        Q->candq[n] = q;
+        sum += q;
+        n++;
+    }
+    *W = sum;
+    *n_out = n;
+    return a;
+}
+
+static int closes_all(const orc_query *Q, int i, const int32_t *tau, int a, int32_t v)
+{
+    const orc_plan *p = &Q->plan;
+    for (int b = 0; b < p->nback[i]; ++b)
+        if (b != a && !is_neighbour(Q->off, Q->cols, tau[p->back[i][b]], v)) return 0;
+    return 1;
+}
+
+/* Sector model of an anchor-draw step: the single-backward draw on the anchor row
+ * plus, per other backward vertex, one offsets sector and one membership search. */
+static uint64_t anchor_sectors(const orc_query *Q, int i, const int32_t *tau, int a)
+{
+    const orc_plan *p = &Q->plan;
+    int32_t anchor = tau[p->back[i][a]];
+    int64_t d = Q->off[anchor + 1] - Q->off[anchor];
+    uint64_t s = 1 + (uint64_t)(i - 1) * sec_search(d, 4);
+    if (Q->use_approx[i]) s += sec_search(d, 8) + 1;
+    s += 1;
+    for (int b = 0; b < p->nback[i]; ++b) {
+        if (b == a) continue;
+        int32_t u = tau[p->back[i][b]];
+        s += 1 + sec_search(Q->off[u + 1] - Q->off[u], 4);
+    }
+    return s;
+}
+
 /* Algorithmic-sector model of one step (a count of 32-byte sectors the step must
  * touch with no reuse; see the design notes):
  *   step 1: search over the (nv+1)-entry running-weight array (+1 for q(v_1));
@@ -634,6 +699,21 @@ double orc_trial(const orc_query *Q, uint64_t t, int32_t tau[ORC_MAXK], uint8_t 
             v = (int32_t)lo;
             q = step_weight(Q, 0, v);
             sec += step_sectors(Q, i, tau, 0);
+        } else if (Q->anchor && p->nback[i] >= 2) {
+            int64_t n;
+            int a = anchor_candidates(Q, i, tau, &W, &n);
+            sec += anchor_sectors(Q, i, tau, a);
+            if (n == 0 || W == 0) { X = 0.0; goto done; }
+            uint64_t r = orc_draw_below(W, t, (uint64_t)(i + 1), ORC_STREAM_TRIAL, Q->seed);
+            uint64_t run = 0;
+            int64_t c = 0;
+            for (c = 0; c < n; ++c) {
+                run += Q->candq[c];
+                if (run > r) break;
+            }
+            v = Q->cand[c];
+            q = Q->candq[c];
+            if (!closes_all(Q, i, tau, a, v)) { X = 0.0; goto done; }
         } else {
             int64_t n = build_candidates(Q, i, tau, &W);
             sec += step_sectors(Q, i, tau, n);
@@ -927,7 +1007,10 @@ static void enum_rec(const orc_query *Q, int i, int32_t *tau, long double p, dou
         return;
     }
     uint64_t W;
-    int64_t n = build_candidates(Q, i, tau, &W);
+    int64_t n;
+    int a = -1;
+    if (Q->anchor && pl->nback[i] >= 2) a = anchor_candidates(Q, i, tau, &W, &n);
+    else n = build_candidates(Q, i, tau, &W);
     if (n == 0 || W == 0) return;
     int32_t *c = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
     uint64_t *cq = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)n);
@@ -935,6 +1018,7 @@ static void enum_rec(const orc_query *Q, int i, int32_t *tau, long double p, dou
     memcpy(cq, Q->candq, sizeof(uint64_t) * (size_t)n);
     for (int64_t j = 0; j < n; ++j) {
         if (cq[j] == 0) continue;
+        if (a >= 0 && !closes_all(Q, i, tau, a, c[j])) continue;   /* a failed trial: X = 0 */
         tau[i] = c[j];
         enum_rec(Q, i + 1, tau, p * (long double)cq[j] / (long double)W,
                  X * ((double)W / (double)cq[j]), m1, m2, nsucc);

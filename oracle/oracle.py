@@ -80,7 +80,7 @@ def lib():
         L.orc_query_create.restype = C.c_void_p
         L.orc_query_create_terms.argtypes = L.orc_query_create.argtypes + [C.c_int32]
         L.orc_query_create_terms.restype = C.c_void_p
-        L.orc_query_create_ex.argtypes = L.orc_query_create.argtypes + [C.c_int32, C.c_int32]
+        L.orc_query_create_ex.argtypes = L.orc_query_create.argtypes + [C.c_int32, C.c_int32, C.c_int32]
         L.orc_query_create_ex.restype = C.c_void_p
         L.orc_orient.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         L.orc_orient.restype = C.c_int64
@@ -251,7 +251,8 @@ class Query:
     """One pattern query on one graph: keeps the oracle's per-query state."""
 
     def __init__(self, off, cols, k, edges, *, nsum=None, hits=None, graph_seed=1,
-                 c_min=2.0 ** -10, mode=MODE_AUTO, beta=0.8, seed=1, terms=0, oriented=False):
+                 c_min=2.0 ** -10, mode=MODE_AUTO, beta=0.8, seed=1, terms=0, oriented=False,
+                 anchor=False):
         self.off = np.ascontiguousarray(off, dtype=np.int64)
         self.cols = np.ascontiguousarray(cols, dtype=np.int32)
         if nsum is None or hits is None:
@@ -262,7 +263,8 @@ class Query:
         self.k = k
         self._h = lib().orc_query_create_ex(len(self.off) - 1, _ptr(self.off), _ptr(self.cols),
                                             _ptr(self.nsum), _ptr(self.hits), c_min, k,
-                                            len(self._flat) // 2, p, mode, beta, seed, terms, int(oriented))
+                                            len(self._flat) // 2, p, mode, beta, seed, terms, int(oriented),
+                                            int(anchor))
         if not self._h:
             raise ValueError("invalid pattern or out of memory")
 

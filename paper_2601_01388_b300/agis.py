@@ -41,7 +41,7 @@ class Opts(C.Structure):
     _fields_ = [("eps", C.c_double), ("delta", C.c_double), ("beta", C.c_double),
                 ("mode", C.c_int32), ("terms", C.c_int32), ("seed", C.c_uint64),
                 ("min_trials", C.c_uint64), ("max_trials", C.c_uint64),
-                ("chunk_trials", C.c_uint64)]
+                ("chunk_trials", C.c_uint64), ("anchor", C.c_int32), ("reserved", C.c_int32)]
 
 
 class Result(C.Structure):

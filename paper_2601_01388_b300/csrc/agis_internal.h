@@ -37,9 +37,11 @@ struct DevStep {
     const uint64_t *pref;       // step 0: inclusive prefix over vertices; |B| = 1: row prefix
 };
 
+constexpr int32_t kFlagAnchor = 1;   // DevQuery::flags: anchor draw on several-backward steps
+
 struct DevQuery {
     int32_t k;
-    int32_t pad;
+    int32_t flags;
     uint64_t seed;
     uint64_t W1;                // total step-1 weight (f_approx sum or nnz)
     DevStep step[kMaxK];

@@ -84,6 +84,7 @@ int check_opts(const agis_opts *o)
     if (!o) return AGIS_ERR_ARG;
     if (o->mode < 0 || o->mode > 2) return AGIS_ERR_ARG;
     if (o->terms < 0 || o->terms > 7) return AGIS_ERR_ARG;
+    if ((o->anchor != 0 && o->anchor != 1) || o->reserved != 0) return AGIS_ERR_ARG;
     if (o->chunk_trials == 0 || o->chunk_trials % kTile != 0) return AGIS_ERR_ARG;
     if (o->max_trials == 0) return AGIS_ERR_ARG;
     if (o->eps > 0.0 && !(o->delta > 0.0 && o->delta < 1.0)) return AGIS_ERR_ARG;
@@ -176,6 +177,7 @@ int make_dev_query(agis_graph *g, const agis_pattern *p, const agis_opts *o, Dev
     if (rc != AGIS_OK) return rc;
     std::memset(dq, 0, sizeof(*dq));
     dq->k = p->k;
+    dq->flags = o->anchor ? kFlagAnchor : 0;
     dq->seed = o->seed;
     const double t0 = now_s();
     bool built = false;
@@ -197,7 +199,7 @@ int make_dev_query(agis_graph *g, const agis_pattern *p, const agis_opts *o, Dev
         // a row-prefix table makes single-backward draws a search; when the full table
         // (8 B per CSR entry) is past the budget only the highest-degree rows get one
         // and the sampler scans the other anchor rows
-        const bool rowp = i > 0 && p->nback[i] == 1;
+        const bool rowp = i > 0 && (p->nback[i] == 1 || o->anchor);
         int32_t cfg[4];
         effective_cfg(p, i, o->terms, g->oriented, cfg);
         rc = build_weight_table(g, cfg, i == 0, rowp, &t);

@@ -522,6 +522,35 @@ __device__ uint32_t filter_list(const int32_t *L, uint32_t n, const int32_t *R, 
 
 // Alg. 3 for trial t of query Q; all 32 lanes call it together.  tau_s is the
 // warp's shared-memory copy of the trajectory.
+// Anchor draw: the drawn v must also be a neighbour of every backward vertex other
+// than the anchor (jb); lane b tests backward vertex b.
+__device__ __forceinline__ bool closes_all(const GraphView &g, const DevStep &S, const int32_t *tau_s, int jb,
+                                           int32_t v, int lane)
+{
+    bool ok = true;
+    if (lane < S.nb && S.back[lane] != jb) {
+        const int32_t u = tau_s[S.back[lane]];
+        const uint32_t *ub = bits_of(g, u);
+        const int64_t s0 = __ldg(g.off + u);
+        ok = ub ? bit_test(ub, v) : row_find(g.cols + s0, __ldg(g.off + u + 1) - s0, v) >= 0;
+    }
+    return __all_sync(kFull, ok);
+}
+
+// sector model of the closing checks: per other backward vertex, its offsets and one
+// membership search in its row
+__device__ __forceinline__ uint64_t closing_sectors(const GraphView &g, const DevStep &S, const int32_t *tau_s,
+                                                    int jb)
+{
+    uint64_t s = 0;
+    for (int b = 0; b < S.nb; ++b) {
+        if (S.back[b] == jb) continue;
+        const int32_t u = tau_s[S.back[b]];
+        s += 1 + sec_search(__ldg(g.off + u + 1) - __ldg(g.off + u), 4);
+    }
+    return s;
+}
+
 __device__ TrialOut run_trial(const GraphView &g, const DevQuery &Q, uint64_t t, int32_t *tau_s,
                               const WarpSets &ws, const uint64_t *top, int lane)
 {
@@ -537,15 +566,27 @@ __device__ TrialOut run_trial(const GraphView &g, const DevQuery &Q, uint64_t t,
         uint64_t W = 0, qv = 0;
         int32_t v = -1;
         STEP_T0
-        // a single-backward step searches its anchor row's prefix when it has one
-        // (always under f_uniform, whose prefix is the position)
+        // the anchor draw proposes from the shortest backward row (first on ties) and
+        // checks the closing edges afterwards, instead of building S
+        const bool anch = i > 0 && S.nb >= 2 && (Q.flags & kFlagAnchor);
+        int jb = i > 0 ? S.back[0] : 0;
+        if (anch) {
+            int64_t best = -1;
+            for (int b = 0; b < S.nb; ++b) {
+                const int32_t u = tau_s[S.back[b]];
+                const int64_t len = __ldg(g.off + u + 1) - __ldg(g.off + u);
+                if (best < 0 || len < best) { best = len; jb = S.back[b]; }
+            }
+        }
+        // a single-backward (or anchor-draw) step searches its row's prefix when it
+        // has one (always under f_uniform, whose prefix is the position)
         bool direct = false;
         const uint64_t *Prow = nullptr;
-        if (i > 0 && S.nb == 1) {
+        if (i > 0 && (S.nb == 1 || anch)) {
             if (!S.approx) {
                 direct = true;
             } else if (S.pref) {
-                const int32_t a = tau_s[S.back[0]];
+                const int32_t a = tau_s[jb];
                 if (S.rp_mode == 1) {
                     Prow = S.pref + __ldg(g.off + a);
                     direct = true;
@@ -570,12 +611,12 @@ __device__ TrialOut run_trial(const GraphView &g, const DevQuery &Q, uint64_t t,
             cur = -1;
             STEP_T1(0)
         } else if (direct) {
-            // ---- one backward neighbour: S = N(a) \ tau
-            const int jb = S.back[0];
+            // ---- one backward neighbour: S = N(a) \ tau (anchor draw: the proposal set)
             const int32_t a = tau_s[jb];
             const int64_t a_start = __ldg(g.off + a);
             const int64_t d = __ldg(g.off + a + 1) - a_start;
             sec += 1 + (uint64_t)(i - 1) * sec_search(d, 4) + (S.approx ? sec_search(d, 8) + 1 : 0) + 1;
+            if (anch) sec += closing_sectors(g, S, tau_s, jb);
             // trajectory members inside a's row (lane j checks tau_j): excluded by
             // vertex id, so a hub row needs one bitmap probe and no search
             bool member = false;
@@ -601,6 +642,7 @@ __device__ TrialOut run_trial(const GraphView &g, const DevQuery &Q, uint64_t t,
             v = __ldg(g.cols + a_start + pos);
             qv = S.approx ? __ldg(S.q + v) : 1u;
             cur = -1;
+            if (anch && !closes_all(g, S, tau_s, jb, v, lane)) { out.sectors = sec; return out; }
             STEP_T1(1)
         } else {
             // ---- several backward neighbours (or one, with no row-prefix table):
@@ -625,15 +667,19 @@ __device__ TrialOut run_trial(const GraphView &g, const DevQuery &Q, uint64_t t,
                 search_sec += row_check_sectors(da, o_len[n_other]);
                 ++n_other;
             }
-            if (S.nb == 1) {
+            // an anchor draw filters only trajectory members here; the other rows are
+            // checked for the drawn vertex alone
+            const int n_filter = anch ? 0 : n_other;
+            if (S.nb == 1 || anch) {
                 // the cost model counts the method's single-backward draw, whichever way it runs
                 sec += 1 + (uint64_t)(i - 1) * sec_search(da, 4) + (S.approx ? sec_search(da, 8) + 1 : 0) + 1;
+                if (anch) sec += closing_sectors(g, S, tau_s, jb);
             } else {
                 sec += (uint64_t)S.nb + (uint64_t)((4 * da + 31) / 32) + search_sec;
             }
             // S of the previous step is reusable when this step's backward set is the
             // previous one plus the previous vertex: S_i = S_{i-1} & N(v_{i-1})
-            const bool reuse = S.inc && cur >= 0;
+            const bool reuse = S.inc && cur >= 0 && !anch;
             const uint32_t n_src = reuse ? n_cur : (uint32_t)da;
             bool listed = false;
             int nxt = reuse ? 1 - cur : 0;
@@ -642,7 +688,7 @@ __device__ TrialOut run_trial(const GraphView &g, const DevQuery &Q, uint64_t t,
             if (ws.cap > 0 && (reuse || da < 0x7fffffffll)) {
                 const int32_t *src = reuse ? ws.xs[cur] : g.cols + a_start;
                 const int tau_n = reuse ? 0 : i;
-                const int passes = reuse ? 1 : (n_other > 0 ? n_other : 1);
+                const int passes = reuse ? 1 : (n_filter > 0 ? n_filter : 1);
                 for (int pss = 0; pss < passes; ++pss) {
                     const int32_t *R = nullptr;
                     const uint32_t *Rb = nullptr;
@@ -652,7 +698,7 @@ __device__ TrialOut run_trial(const GraphView &g, const DevQuery &Q, uint64_t t,
                         R = g.cols + __ldg(g.off + u);
                         m = __ldg(g.off + u + 1) - __ldg(g.off + u);
                         Rb = bits_of(g, u);
-                    } else if (n_other > 0) {
+                    } else if (n_filter > 0) {
                         R = g.cols + o_start[pss];
                         m = o_len[pss];
                         Rb = o_bits[pss];
@@ -672,7 +718,7 @@ __device__ TrialOut run_trial(const GraphView &g, const DevQuery &Q, uint64_t t,
                 listed = n <= ws.cap;
             }
             if (listed) {
-                if (S.approx && S.nb > 1) sec += n;
+                if (S.approx && S.nb > 1 && !anch) sec += n;
                 W = Wl;
                 cur = nxt;
                 n_cur = n;
@@ -681,6 +727,10 @@ __device__ TrialOut run_trial(const GraphView &g, const DevQuery &Q, uint64_t t,
                 const int64_t j = warp_find(ws.pw[cur], n, r, 0u, 0, 0, nullptr, lane);
                 v = ws.xs[cur][j];
                 qv = ws.pw[cur][j] - (j > 0 ? ws.pw[cur][j - 1] : 0);
+                if (anch) {
+                    cur = -1;
+                    if (!closes_all(g, S, tau_s, jb, v, lane)) { out.sectors = sec; return out; }
+                }
                 X = X * ((double)W / (double)qv);
                 STEP_T1(reuse ? 3 : 2)
                 __syncwarp();
@@ -703,7 +753,7 @@ __device__ TrialOut run_trial(const GraphView &g, const DevQuery &Q, uint64_t t,
 #pragma unroll
                 for (int u = 0; u < U; ++u)
                     wtv[u] = window_weight(g, S, tau_s, i, a_start, da, (w0 + u) * 32 + lane, o_start,
-                                           o_len, o_bits, n_other, okv[u], xv[u]);
+                                           o_len, o_bits, n_filter, okv[u], xv[u]);
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     const int64_t w = w0 + u;
@@ -721,7 +771,7 @@ __device__ TrialOut run_trial(const GraphView &g, const DevQuery &Q, uint64_t t,
                     }
                 }
             }
-            if (S.approx && S.nb > 1) sec += nsurv;
+            if (S.approx && S.nb > 1 && !anch) sec += nsurv;
             W = running;
             if (W == 0) { out.sectors = sec; return out; }
             const uint64_t r = draw_below(W, t, (uint64_t)(i + 1), kStreamTrial, Q.seed);
@@ -740,7 +790,7 @@ __device__ TrialOut run_trial(const GraphView &g, const DevQuery &Q, uint64_t t,
                     bool ok;
                     int32_t x;
                     const uint64_t wt = window_weight(g, S, tau_s, i, a_start, da, w * 32 + lane,
-                                                      o_start, o_len, o_bits, n_other, ok, x);
+                                                      o_start, o_len, o_bits, n_filter, ok, x);
                     const uint64_t incl = warp_incl_scan(wt, lane);
                     const uint64_t wtot = __shfl_sync(kFull, incl, 31);
                     if (run2 + wtot > r) {
@@ -754,7 +804,10 @@ __device__ TrialOut run_trial(const GraphView &g, const DevQuery &Q, uint64_t t,
                 }
             }
         }
-        if (i > 0 && !direct) { STEP_T1(4) }
+        if (i > 0 && !direct) {
+            STEP_T1(4)
+            if (anch && !closes_all(g, S, tau_s, jb, v, lane)) { out.sectors = sec; return out; }
+        }
         X = X * ((double)W / (double)qv);
         __syncwarp();
         if (lane == 0) tau_s[i] = v;

@@ -65,7 +65,7 @@ size_t extra_bytes(agis_graph *g, const agis_pattern &p, const agis_opts &o)
         effective_cfg(&p, i, o.terms, g->oriented, cfg);
         auto &f = need[cfg_key(cfg)];
         f.first = f.first || i == 0;
-        f.second = f.second || (i > 0 && p.nback[i] == 1);
+        f.second = f.second || (i > 0 && (p.nback[i] == 1 || o.anchor));
     }
     size_t extra = 0;
     for (const auto &kv : need) {
