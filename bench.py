@@ -497,7 +497,7 @@ def ablation(agis, g, cap_log2=28):
 
 # ------------------------------------------------------------------ concentration
 
-def concentration_run(agis, g, cap_log2=30):
+def concentration_run(agis, g, cap_log2=28):
     """Sec. 6.3 on the resident graph: every connected 4-vertex (6) and 5-vertex (21)
     pattern as one batch, each to +-1% (95%); concentrations of the non-induced
     subgraph counts, and the variation distance between two independently seeded
@@ -528,7 +528,7 @@ def concentration_run(agis, g, cap_log2=30):
 
 # ------------------------------------------------------------------ orientation for cliques
 
-def cliques_oriented(agis, g, cap_log2=32):
+def cliques_oriented(agis, g, cap_log2=30):
     """Sec. 5.4's orientation for clique patterns on the resident graph: time to
     orient and preprocess the DAG, then time and trials to +-1% (95%) for the 4-, 5-
     and 6-clique on the undirected graph and on the orientation (same seeds)."""
@@ -563,7 +563,7 @@ def cliques_oriented(agis, g, cap_log2=32):
 
 # ------------------------------------------------------------------ anchor draw
 
-def anchor_vs_exact(agis, g, names, cap_log2=32):
+def anchor_vs_exact(agis, g, names, cap_log2=30):
     """Time and trials to +-1% (95%) for each pattern with S_tau built as in Alg. 3
     and with the anchor draw (proposal from the shortest backward row, closing edges
     checked afterwards), same seeds."""

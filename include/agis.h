@@ -70,8 +70,9 @@ typedef struct {
     double beta;            /* decision threshold (AUTO mode)                          */
     int32_t mode;           /* agis_mode                                               */
     int32_t terms;          /* factors of Eq. probability_function kept: bit 0 T[F1],
-                               bit 1 T[I1], bit 2 T[F2]; 0 = all (the method). Others
-                               give the incremental versions of the Sec. 6.2 ablation */
+                               bit 1 T[I1], bit 2 T[F2]; 0 = all (the method).  1, 3, 5
+                               give the incremental versions of the Sec. 6.2 ablation;
+                               T[F1] must be kept (else ARG)                           */
     uint64_t seed;          /* Philox key of this query's trials                       */
     uint64_t min_trials;    /* Alg. 1 is not consulted before this many trials         */
     uint64_t max_trials;    /* hard budget; with eps <= 0 exactly this many run        */

@@ -444,6 +444,9 @@ orc_query *orc_query_create_ex(int64_t nv, const int64_t *off, const int32_t *co
     Q->anchor = anchor != 0;
     if (orc_plan_compile(k, ne, edges, &Q->plan) != 0) { free(Q); return NULL; }
     if (oriented && ne != k * (k - 1) / 2) { free(Q); return NULL; }
+    /* T[F1] stays in every incremental version: without it a vertex of degree 0
+     * would reach the nsum/d factor of T[F2] */
+    if (terms < 0 || terms > 7 || (terms != 0 && !(terms & 1))) { free(Q); return NULL; }
     for (int i = 0; i < Q->plan.k; ++i) Q->wb[i] = oriented ? 0 : Q->plan.nback[i];
     if (terms != 0) {
         for (int i = 0; i < Q->plan.k; ++i) {

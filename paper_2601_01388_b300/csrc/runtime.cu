@@ -83,7 +83,9 @@ int check_opts(const agis_opts *o)
 {
     if (!o) return AGIS_ERR_ARG;
     if (o->mode < 0 || o->mode > 2) return AGIS_ERR_ARG;
-    if (o->terms < 0 || o->terms > 7) return AGIS_ERR_ARG;
+    // T[F1] stays in every version (Sec. 6.2 adds terms to it): without it a vertex of
+    // degree 0 would reach the nsum/d factor of T[F2]
+    if (o->terms < 0 || o->terms > 7 || (o->terms != 0 && !(o->terms & 1))) return AGIS_ERR_ARG;
     if ((o->anchor != 0 && o->anchor != 1) || o->reserved != 0) return AGIS_ERR_ARG;
     if (o->chunk_trials == 0 || o->chunk_trials % kTile != 0) return AGIS_ERR_ARG;
     if (o->max_trials == 0) return AGIS_ERR_ARG;

@@ -13,7 +13,7 @@ from paper_2601_01388_b300 import inputs as I
 from tests.test_oracle_pins import TINY_GRAPHS, falling
 
 CMIN = 2.0 ** -10
-MASKS = (1, 2, 3, 4, 5, 6, 7)
+MASKS = (1, 3, 5, 7)     # T[F1] is kept in every version
 
 
 def masked_cfg(cfg, terms):
@@ -62,6 +62,13 @@ def test_masked_sampler_unbiased(oracle_mod, gname, terms):
         mean, _, nsucc = q.enumerate()
         assert nsucc == truth
         assert mean == pytest.approx(truth, rel=1e-12, abs=1e-12), (name, terms)
+
+
+def test_masks_without_first_term_rejected(oracle_mod):
+    off, cols = I.gnp_graph(12, 0.4, 1)
+    for bad in (2, 4, 6, 8, -1):
+        with pytest.raises(ValueError):
+            oracle_mod.Query(off, cols, *I.PATTERNS["triangle"], terms=bad)
 
 
 def test_full_mask_is_the_method(oracle_mod):
@@ -198,7 +205,7 @@ def test_masked_estimate_sums(agis, oracle_mod, rmat12):
 @pytest.mark.gpu
 def test_bad_terms_rejected(agis, rmat12):
     g = rmat12[2]
-    for bad in (-1, 8):
+    for bad in (-1, 2, 4, 6, 8):
         with pytest.raises(agis.AgisError) as e:
             agis.estimate(g, agis.Pattern(*I.PATTERNS["triangle"]), agis.default_opts(terms=bad))
         assert e.value.status == agis.ERR_ARG
