@@ -39,7 +39,6 @@ sys.path.insert(0, ROOT)
 METRIC = "samples/s & time-to-±1% err (95% CI), batched/served vs plain, 1 B300"
 PATTERN_NAMES = ["4-clique", "5-cycle", "house", "5-clique"]
 CMIN = 2.0 ** -10
-TILE = 1024
 
 
 def parse_args():
@@ -599,7 +598,7 @@ def run_gpu(args, world, rank, local):
 
     names = [n for n in args.patterns.split(",") if n]
     trials = 1 << args.log2_trials
-    ntiles = (trials + TILE - 1) // TILE
+    ntiles = (trials + agis.TILE - 1) // agis.TILE
     off, cols, t_gen = make_workload(args.scale)
 
     pool = None

@@ -261,8 +261,12 @@ int agis_dump_trials(agis_graph *g, const agis_pattern *p, const agis_opts *opts
                      uint64_t first, uint64_t count, int32_t *emb, uint8_t *hit, double *x,
                      uint64_t *sectors);
 
+/* agis_tile_trials: trials per tile, the unit of work and of the fixed-order FP64
+ * reduction (a power of two dividing 1024; set when the library is built). */
+int agis_tile_trials(void);
+
 /* agis_sample_device: fixed-budget sampling with all buffers on the device:
- * trials [first, first + ntiles*1024) of the query, per-tile sums written to
+ * trials [first, first + ntiles*T) of the query, T = agis_tile_trials(), per-tile sums written to
  * tile_out (device, ntiles * 4 uint64 words per tile: hits, sectors, then the FP64
  * sum X and sum X^2 bit patterns).  Enqueued on ctx's stream, no host sync.
  * Errors: ARG, STATE, NOMEM, CUDA. */

@@ -24,7 +24,6 @@ _lib = C.CDLL(LIB_PATH)
 OK, ERR_ARG, ERR_NOMEM, ERR_CUDA, ERR_GRAPH, ERR_PATTERN, ERR_TIMEOUT, ERR_BUSY, ERR_STATE = \
     0, -1, -2, -3, -4, -5, -6, -7, -8
 MODE_AUTO, MODE_APPROX, MODE_UNIFORM = 0, 1, 2
-TILE = 1024
 
 EXPORTS = [
     "agis_status_str", "agis_default_opts", "agis_create", "agis_destroy", "agis_graph_load_csr",
@@ -32,7 +31,7 @@ EXPORTS = [
     "agis_graph_row_prefix", "agis_graph_orient", "agis_graph_is_oriented", "agis_graph_set_memory_policy", "agis_graph_validate", "agis_graph_copy_csr", "agis_graph_drop_tables", "agis_graph_free", "agis_graph_generate_rmat", "agis_graph_generate_chunglu",
     "agis_pattern_create", "agis_pattern_info", "agis_pattern_decide", "agis_pattern_free",
     "agis_estimate", "agis_estimate_batch", "agis_autotune", "agis_dump_trials", "agis_sample_device",
-    "agis_prepare", "agis_z_of_delta", "agis_kernel_launches", "agis_prefix_sum_u64_noalloc", "agis_probe_random_read", "agis_step_timers", "agis_server_create", "agis_server_submit", "agis_server_poll",
+    "agis_prepare", "agis_tile_trials", "agis_z_of_delta", "agis_kernel_launches", "agis_prefix_sum_u64_noalloc", "agis_probe_random_read", "agis_step_timers", "agis_server_create", "agis_server_submit", "agis_server_poll",
     "agis_server_stats", "agis_server_destroy",
 ]
 
@@ -88,6 +87,7 @@ _sig = {
     "agis_prepare": ([VP, VP, P(Opts)], C.c_int),
     "agis_autotune": ([VP, C.c_int, P(VP), P(Opts), C.c_uint64, P(C.c_int32)], C.c_int),
     "agis_z_of_delta": ([C.c_double], C.c_double),
+    "agis_tile_trials": ([], C.c_int),
     "agis_kernel_launches": ([], C.c_uint64),
     "agis_prefix_sum_u64_noalloc": ([VP, C.c_int64, VP, VP], C.c_int),
     "agis_probe_random_read": ([VP, C.c_uint64, C.c_uint64, C.c_uint64, VP, VP], C.c_int),
@@ -104,6 +104,9 @@ for _name, (_args, _res) in _sig.items():
         continue
     _f.argtypes = _args
     _f.restype = _res
+
+
+TILE = int(_lib.agis_tile_trials())    # trials per tile (the build's tile size)
 
 
 class AgisError(RuntimeError):

@@ -19,7 +19,11 @@
 namespace agis {
 
 constexpr int kMaxK = 8;
-constexpr int kTile = 1024;          // trials per work item (one CTA at a time)
+#ifndef AGIS_TILE
+#define AGIS_TILE 1024
+#endif
+constexpr int kTile = AGIS_TILE;     // trials per work item (one CTA at a time)
+static_assert(kTile >= 32 && kTile <= 1024 && (kTile & (kTile - 1)) == 0, "tile: power of two in [32, 1024]");
 constexpr int kBlock = 256;          // threads per CTA of the sampler
 constexpr int kWarps = kBlock / 32;
 constexpr uint64_t kStreamTrial = 1; // Philox counter word 2 of a trial draw

@@ -87,7 +87,7 @@ int check_opts(const agis_opts *o)
     // degree 0 would reach the nsum/d factor of T[F2]
     if (o->terms < 0 || o->terms > 7 || (o->terms != 0 && !(o->terms & 1))) return AGIS_ERR_ARG;
     if ((o->anchor != 0 && o->anchor != 1) || o->reserved != 0) return AGIS_ERR_ARG;
-    if (o->chunk_trials == 0 || o->chunk_trials % kTile != 0) return AGIS_ERR_ARG;
+    if (o->chunk_trials == 0 || o->chunk_trials % 1024 != 0) return AGIS_ERR_ARG;
     if (o->max_trials == 0) return AGIS_ERR_ARG;
     if (o->eps > 0.0 && !(o->delta > 0.0 && o->delta < 1.0)) return AGIS_ERR_ARG;
     return AGIS_OK;
@@ -477,6 +477,11 @@ extern "C" const char *agis_status_str(int s)
     case AGIS_ERR_STATE: return "invalid state";
     default: return "unknown status";
     }
+}
+
+extern "C" int agis_tile_trials(void)
+{
+    return kTile;
 }
 
 extern "C" void agis_default_opts(agis_opts *o)

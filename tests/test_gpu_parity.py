@@ -195,8 +195,9 @@ def test_sample_device_tiles(agis, oracle_mod, graphs):
     torch.cuda.synchronize()
     h, sec, sx, sx2 = agis.tile_sums(out.cpu().numpy().view(np.uint64))
     q = oracle_mod.Query(off, cols, k, edges, nsum=nsum, hits=hits, c_min=CMIN, mode=0, seed=9)
+    T = agis.TILE
     for t in (0, 17, 36):
-        s = q.sums(2048 + 1024 * t, 1024)
+        s = q.sums(2048 + T * t, T)
         assert h[t] == s["hits"] and sec[t] == s["sectors"]
         assert sx[t] == pytest.approx(s["sum_x"], rel=REL, abs=0)
         assert sx2[t] == pytest.approx(s["sum_x2"], rel=REL, abs=0)

@@ -48,7 +48,7 @@ def test_status_strings(agis):
 def test_default_opts(agis):
     o = agis.default_opts()
     assert (o.eps, o.delta, o.beta, o.mode) == (0.1, 0.01, 0.8, 0)
-    assert o.chunk_trials % agis.TILE == 0
+    assert o.chunk_trials % 1024 == 0 and 1024 % agis.TILE == 0
 
 
 def test_z_matches_scipy(agis):
