@@ -121,6 +121,7 @@ struct LaunchBuffers {
     int graph_grid = 0;
     uint64_t generation = 0;       // bumps when device buffers move (graph must be rebuilt)
     uint64_t graph_generation = ~0ull;
+    bool graph_anchor = false;  // the cached graph's kernel node is the anchor-capable instance
 };
 
 }  // namespace agis
@@ -191,11 +192,12 @@ size_t table_bytes(const agis_graph *g, const int32_t cfg[4], bool need_pref, bo
 void free_table(WeightTable &t);
 
 // sample.cu
+// anchor: some staged query uses the anchor draw (selects the kernel instance)
 int launch_sampler(agis_graph *g, LaunchBuffers &lb, int grid, const DumpView *dump,
                    cudaStream_t stream, uint64_t implicit_first, uint64_t implicit_count,
-                   uint64_t *tile_out);
+                   uint64_t *tile_out, bool anchor);
 int add_sampler_node(agis_graph *g, LaunchBuffers &lb, int grid, cudaGraph_t graph,
-                     const cudaGraphNode_t *deps, size_t ndeps, cudaGraphNode_t *node);
+                     const cudaGraphNode_t *deps, size_t ndeps, cudaGraphNode_t *node, bool anchor);
 int sampler_occupancy(int *blocks_per_sm);
 
 // runtime.cu

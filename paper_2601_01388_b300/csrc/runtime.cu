@@ -346,6 +346,13 @@ size_t stage_items(LaunchBuffers &lb, std::vector<QueryRun *> &runs, const std::
 }
 
 // One epoch by plain stream launches.
+static bool any_anchor(const std::vector<QueryRun *> &runs)
+{
+    for (const QueryRun *r : runs)
+        if (r->dq.flags & kFlagAnchor) return true;
+    return false;
+}
+
 int run_epoch_direct(agis_graph *g, std::vector<QueryRun *> &runs, const std::vector<uint64_t> &ntiles,
                      size_t total)
 {
@@ -361,7 +368,7 @@ int run_epoch_direct(agis_graph *g, std::vector<QueryRun *> &runs, const std::ve
     AGIS_CUDA_TRY(cudaMemcpyAsync(lb.d_counter, lb.h_counter, 2 * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
     const int grid = grid_for(g, n);
     if ((rc = ensure_scratch(g, lb, grid)) != AGIS_OK) return rc;
-    rc = launch_sampler(g, lb, grid, nullptr, st, 0, 0, nullptr);
+    rc = launch_sampler(g, lb, grid, nullptr, st, 0, 0, nullptr, any_anchor(runs));
     if (rc != AGIS_OK) return rc;
     AGIS_CUDA_TRY(cudaMemcpyAsync(lb.h_out, lb.d_out, sizeof(uint64_t) * 4 * n, cudaMemcpyDeviceToHost, st));
     AGIS_CUDA_TRY(cudaStreamSynchronize(st));
@@ -383,7 +390,8 @@ int run_epoch_graph(agis_graph *g, std::vector<QueryRun *> &runs, const std::vec
     lb.h_counter[1] = (uint32_t)n;
     const int grid = grid_for(g, (size_t)g->ctx->sm_count * 64);
     if ((rc = ensure_scratch(g, lb, grid)) != AGIS_OK) return rc;
-    if (!lb.exec || lb.graph_generation != lb.generation || lb.graph_grid != grid) {
+    const bool anchor = any_anchor(runs);
+    if (!lb.exec || lb.graph_generation != lb.generation || lb.graph_grid != grid || lb.graph_anchor != anchor) {
         if (lb.exec) cudaGraphExecDestroy(lb.exec);
         if (lb.graph) cudaGraphDestroy(lb.graph);
         lb.exec = nullptr;
@@ -395,12 +403,13 @@ int run_epoch_graph(agis_graph *g, std::vector<QueryRun *> &runs, const std::vec
                                                sizeof(WorkItem), cudaMemcpyHostToDevice));
         AGIS_CUDA_TRY(cudaGraphAddMemcpyNode1D(&lb.n_h2d_c, lb.graph, &lb.n_h2d_i, 1, lb.d_counter, lb.h_counter,
                                                2 * sizeof(uint32_t), cudaMemcpyHostToDevice));
-        rc = add_sampler_node(g, lb, grid, lb.graph, &lb.n_h2d_c, 1, &lb.n_kernel);
+        rc = add_sampler_node(g, lb, grid, lb.graph, &lb.n_h2d_c, 1, &lb.n_kernel, anchor);
         if (rc != AGIS_OK) return rc;
         AGIS_CUDA_TRY(cudaGraphAddMemcpyNode1D(&lb.n_d2h, lb.graph, &lb.n_kernel, 1, lb.h_out, lb.d_out,
                                                4 * sizeof(uint64_t), cudaMemcpyDeviceToHost));
         AGIS_CUDA_TRY(cudaGraphInstantiate(&lb.exec, lb.graph, 0));
         lb.graph_generation = lb.generation;
+        lb.graph_anchor = anchor;
         lb.graph_grid = grid;
     }
     AGIS_CUDA_TRY(cudaGraphExecMemcpyNodeSetParams1D(lb.exec, lb.n_h2d_q, lb.d_queries, lb.h_queries,
@@ -670,7 +679,7 @@ extern "C" int agis_dump_trials(agis_graph *g, const agis_pattern *p, const agis
     cudaMemcpyAsync(lb.d_counter, lb.h_counter, 2 * sizeof(uint32_t), cudaMemcpyHostToDevice, st);
     const int grid = grid_for(g, ntiles);
     if (rc == AGIS_OK) rc = ensure_scratch(g, lb, grid);
-    if (rc == AGIS_OK) rc = launch_sampler(g, lb, grid, &dv, st, first, count, nullptr);
+    if (rc == AGIS_OK) rc = launch_sampler(g, lb, grid, &dv, st, first, count, nullptr, true);
     cudaError_t e = cudaStreamSynchronize(st);
     if (rc == AGIS_OK && e != cudaSuccess) rc = AGIS_ERR_CUDA;
     if (rc == AGIS_OK && emb && cudaMemcpy(emb, dv.emb, sizeof(int32_t) * kMaxK * c, cudaMemcpyDeviceToHost) != cudaSuccess) rc = AGIS_ERR_CUDA;
@@ -704,7 +713,8 @@ extern "C" int agis_sample_device(agis_graph *g, const agis_pattern *p, const ag
     AGIS_CUDA_TRY(cudaMemcpyAsync(lb.d_counter, counter, sizeof(counter), cudaMemcpyHostToDevice, st));
     const int grid = grid_for(g, ntiles);
     if ((rc = ensure_scratch(g, lb, grid)) != AGIS_OK) return rc;
-    return launch_sampler(g, lb, grid, nullptr, st, first, ntiles * kTile, tile_out);
+    return launch_sampler(g, lb, grid, nullptr, st, first, ntiles * kTile, tile_out,
+                          (dq.flags & kFlagAnchor) != 0);
 }
 
 extern "C" int agis_prepare(agis_graph *g, const agis_pattern *p, const agis_opts *opts)
@@ -734,9 +744,11 @@ extern "C" int agis_autotune(agis_graph *g, int n, const agis_pattern *const *pa
     if (rc != AGIS_OK) return rc;
     const uint64_t ntiles = (trials_per_query + kTile - 1) / kTile;
     std::vector<DevQuery> dqs((size_t)n);
+    bool anchor = false;
     for (int i = 0; i < n; ++i) {
         if ((rc = check_opts(&opts[i])) != AGIS_OK) return rc;
         if ((rc = make_dev_query(g, patterns[i], &opts[i], &dqs[(size_t)i], nullptr)) != AGIS_OK) return rc;
+        anchor = anchor || (dqs[(size_t)i].flags & kFlagAnchor);
     }
     LaunchBuffers &lb = g->lb;
     const size_t items = (size_t)n * ntiles;
@@ -768,7 +780,7 @@ extern "C" int agis_autotune(agis_graph *g, int n, const agis_pattern *const *pa
             const uint32_t counter[2] = {0u, (uint32_t)items};
             cudaMemcpyAsync(lb.d_counter, counter, sizeof(counter), cudaMemcpyHostToDevice, st);
             cudaEventRecord(e0, st);
-            rc = launch_sampler(g, lb, grid, nullptr, st, 0, 0, nullptr);
+            rc = launch_sampler(g, lb, grid, nullptr, st, 0, 0, nullptr, anchor);
             cudaEventRecord(e1, st);
             if (rc != AGIS_OK) break;
             if (cudaEventSynchronize(e1) != cudaSuccess) { rc = AGIS_ERR_CUDA; break; }

@@ -551,6 +551,7 @@ __device__ __forceinline__ uint64_t closing_sectors(const GraphView &g, const De
     return s;
 }
 
+template <bool kAnchor>
 __device__ TrialOut run_trial(const GraphView &g, const DevQuery &Q, uint64_t t, int32_t *tau_s,
                               const WarpSets &ws, const uint64_t *top, int lane)
 {
@@ -568,7 +569,7 @@ __device__ TrialOut run_trial(const GraphView &g, const DevQuery &Q, uint64_t t,
         STEP_T0
         // the anchor draw proposes from the shortest backward row (first on ties) and
         // checks the closing edges afterwards, instead of building S
-        const bool anch = i > 0 && S.nb >= 2 && (Q.flags & kFlagAnchor);
+        const bool anch = kAnchor && i > 0 && S.nb >= 2 && (Q.flags & kFlagAnchor);
         int jb = i > 0 ? S.back[0] : 0;
         if (anch) {
             int64_t best = -1;
@@ -822,7 +823,9 @@ __device__ TrialOut run_trial(const GraphView &g, const DevQuery &Q, uint64_t t,
 // Work items come from `items`, or, when it is null, are implicit: item j covers
 // trials [implicit_first + 1024 j, ...) of query 0 up to implicit_count trials and
 // writes slot j.  n_items_ptr[0] holds the number of items.
-template <bool kDump>
+// kAnchor: the instance that can run anchor-draw queries (the other one compiles
+// that code away; both give the same results for queries without the flag)
+template <bool kDump, bool kAnchor>
 __global__ void __launch_bounds__(kBlock, AGIS_MIN_BLOCKS) sample_kernel(GraphView g, const DevQuery *__restrict__ queries,
                                                         const WorkItem *__restrict__ items,
                                                         const uint32_t *__restrict__ n_items_ptr,
@@ -903,7 +906,7 @@ __global__ void __launch_bounds__(kBlock, AGIS_MIN_BLOCKS) sample_kernel(GraphVi
             tt = __shfl_sync(kFull, tt, 0);
             if (tt >= it.count) break;
             const uint64_t t = it.first + tt;
-            const TrialOut r = run_trial(g, sq, t, tau_s[warp], ws, s_top, lane);
+            const TrialOut r = run_trial<kAnchor>(g, sq, t, tau_s[warp], ws, s_top, lane);
             if (lane == 0) {
                 xs[tt] = r.x;
                 if (r.hit) atomicAdd(&s_hits, 1u);
@@ -953,7 +956,7 @@ __global__ void __launch_bounds__(kBlock, AGIS_MIN_BLOCKS) sample_kernel(GraphVi
 
 int sampler_occupancy(int *blocks_per_sm)
 {
-    return cuda_status(cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, sample_kernel<false>,
+    return cuda_status(cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, sample_kernel<false, false>,
                                                                     kBlock, 0));
 }
 
@@ -962,29 +965,29 @@ int sampler_occupancy(int *blocks_per_sm)
 // implicit_count > 0 the items are implicit tiles of query 0 (see the kernel).
 int launch_sampler(agis_graph *g, LaunchBuffers &lb, int grid, const DumpView *dump,
                    cudaStream_t stream, uint64_t implicit_first, uint64_t implicit_count,
-                   uint64_t *tile_out)
+                   uint64_t *tile_out, bool anchor)
 {
     GraphView gv{g->off, g->cols, g->nv, g->nnz, g->hub_id, g->hub_bits, g->hub_words, g->rp_base};
     const WorkItem *items = implicit_count ? nullptr : lb.d_items;
     uint64_t *out = tile_out ? tile_out : lb.d_out;
     if (dump) {
         count_launch();
-        sample_kernel<true><<<grid, kBlock, 0, stream>>>(gv, lb.d_queries, items, lb.d_counter + 1,
-                                                         lb.d_counter, out, *dump, implicit_first,
-                                                         implicit_count, (char *)lb.d_scratch, lb.scratch_cap);
+        sample_kernel<true, true><<<grid, kBlock, 0, stream>>>(gv, lb.d_queries, items, lb.d_counter + 1,
+                                                               lb.d_counter, out, *dump, implicit_first,
+                                                               implicit_count, (char *)lb.d_scratch, lb.scratch_cap);
     } else {
         DumpView none{nullptr, nullptr, nullptr, nullptr, 0};
         count_launch();
-        sample_kernel<false><<<grid, kBlock, 0, stream>>>(gv, lb.d_queries, items, lb.d_counter + 1,
-                                                          lb.d_counter, out, none, implicit_first,
-                                                          implicit_count, (char *)lb.d_scratch, lb.scratch_cap);
+        auto *kern = anchor ? sample_kernel<false, true> : sample_kernel<false, false>;
+        kern<<<grid, kBlock, 0, stream>>>(gv, lb.d_queries, items, lb.d_counter + 1, lb.d_counter, out, none,
+                                          implicit_first, implicit_count, (char *)lb.d_scratch, lb.scratch_cap);
     }
     return cuda_status(cudaGetLastError());
 }
 
 // Adds the sampler as a kernel node of a CUDA graph (explicit items, no dump).
 int add_sampler_node(agis_graph *g, LaunchBuffers &lb, int grid, cudaGraph_t graph,
-                     const cudaGraphNode_t *deps, size_t ndeps, cudaGraphNode_t *node)
+                     const cudaGraphNode_t *deps, size_t ndeps, cudaGraphNode_t *node, bool anchor)
 {
     static GraphView gv;
     static DumpView none;
@@ -1008,7 +1011,7 @@ int add_sampler_node(agis_graph *g, LaunchBuffers &lb, int grid, cudaGraph_t gra
     cap = lb.scratch_cap;
     void *args[] = {&gv, &q, &it, &nptr, &ctr, &out, &none, &z0, &z1, &scr, &cap};
     cudaKernelNodeParams p = {};
-    p.func = (void *)sample_kernel<false>;
+    p.func = anchor ? (void *)sample_kernel<false, true> : (void *)sample_kernel<false, false>;
     p.gridDim = dim3(grid);
     p.blockDim = dim3(kBlock);
     p.sharedMemBytes = 0;
