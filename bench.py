@@ -185,16 +185,22 @@ def measured_peaks():
     return 6400.0, "fallback"
 
 
+def kernel_source_hash():
+    """sha256[:16] over the sampler's sources (kernel, shared definitions, RNG)."""
+    h = hashlib.sha256()
+    for f in ("sample.cu", "agis_internal.h", "philox.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2601_01388_b300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def profile_traffic(trials_per_launch):
     """DRAM bytes per trial of the sampler from the committed ncu summary, if it was
     taken on the current kernel source (else None)."""
     path = os.path.join(ROOT, "profiles", "sample_kernel_rmat_s22.md")
-    src = os.path.join(ROOT, "paper_2601_01388_b300", "csrc", "sample.cu")
     if not os.path.exists(path):
         return None
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     text = open(path).read()
-    if f"sample.cu sha256[:16]: {h}" not in text:
+    if f"kernel sources sha256[:16]: {kernel_source_hash()}" not in text:
         return None
     for line in text.splitlines():
         if line.strip().startswith("dram_bytes_per_trial:"):
@@ -543,8 +549,8 @@ def cliques_oriented(agis, g, cap_log2=30):
            "runs": []}
     for name in ("4-clique", "5-clique", "6-clique"):
         p = agis.Pattern(*I.PATTERNS[name])
-        for label, graph in (("undirected", g), ("oriented", o)):
-            opts = agis.default_opts(mode=0, seed=53, eps=0.01, delta=0.05, chunk_trials=1 << 16,
+        for label, graph, anchor in (("undirected", g, 0), ("oriented", o, 0), ("oriented+anchor", o, 1)):
+            opts = agis.default_opts(mode=0, seed=53, anchor=anchor, eps=0.01, delta=0.05, chunk_trials=1 << 16,
                                      min_trials=1 << 16, max_trials=1 << cap_log2)
             graph.drop_tables()
             t0 = time.perf_counter()

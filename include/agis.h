@@ -237,7 +237,7 @@ int agis_pattern_free(agis_pattern *p);
 /* ---- estimation ------------------------------------------------------------
  * agis_estimate: one query, plain per-query launches.  Runs Alg. 3 trials
  * 0, 1, 2, ... (trial t draws step i from Philox4x64-10 counter (t, i, 1, 0), key
- * (seed, 0)) in tiles of 1024 on the device, and evaluates Alg. 1 on host at every
+ * (seed, 0)) in tiles of agis_tile_trials() trials on the device, and evaluates Alg. 1 on host at every
  * chunk_trials checkpoint once min_trials trials are in.  The result is that of the
  * first converged checkpoint, or of max_trials; it is a deterministic function of
  * (graph, pattern, opts).  eps <= 0 runs exactly max_trials trials.

@@ -20,7 +20,7 @@ namespace agis {
 
 constexpr int kMaxK = 8;
 #ifndef AGIS_TILE
-#define AGIS_TILE 1024
+#define AGIS_TILE 256
 #endif
 constexpr int kTile = AGIS_TILE;     // trials per work item (one CTA at a time)
 static_assert(kTile >= 32 && kTile <= 1024 && (kTile & (kTile - 1)) == 0, "tile: power of two in [32, 1024]");

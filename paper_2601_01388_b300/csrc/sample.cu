@@ -1,5 +1,5 @@
 // The sampler: Alg. 3 (structure-informed neighbour sampling) with one warp per
-// trial, persistent CTAs pulling work items (1024-trial tiles of any query) from a
+// trial, persistent CTAs pulling work items (kTile-trial tiles of any query) from a
 // device counter, and a fixed-order FP64 reduction of each tile.
 //
 // Per step i of a trial (tau = v_1..v_{i-1} so far):
@@ -821,7 +821,7 @@ __device__ TrialOut run_trial(const GraphView &g, const DevQuery &Q, uint64_t t,
 }
 
 // Work items come from `items`, or, when it is null, are implicit: item j covers
-// trials [implicit_first + 1024 j, ...) of query 0 up to implicit_count trials and
+// trials [implicit_first + kTile j, ...) of query 0 up to implicit_count trials and
 // writes slot j.  n_items_ptr[0] holds the number of items.
 // kAnchor: the instance that can run anchor-draw queries (the other one compiles
 // that code away; both give the same results for queries without the flag)
