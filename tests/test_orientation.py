@@ -54,6 +54,21 @@ def test_oriented_sampler_counts_cliques(oracle_mod, gname, mode):
         assert mean == pytest.approx(cliques, rel=1e-12, abs=1e-12), (name, gname)
 
 
+@pytest.mark.parametrize("gname", ["gnp10", "gnp12", "k6", "mixed"])
+def test_oriented_anchor_draw_counts_cliques(oracle_mod, gname):
+    """The anchor draw on the orientation: still one trajectory per clique."""
+    off, cols = TINY_GRAPHS[gname]()
+    oo, oc = oracle_mod.orient(off, cols)
+    for name in CLIQUES:
+        k, edges = I.PATTERNS[name]
+        cliques = oracle_mod.bruteforce_count(off, cols, k, edges) // math.factorial(k)
+        for mode in (1, 2):
+            q = oracle_mod.Query(oo, oc, k, edges, mode=mode, oriented=True, anchor=True)
+            mean, _, nsucc = q.enumerate()
+            assert nsucc == cliques
+            assert mean == pytest.approx(cliques, rel=1e-12, abs=1e-12)
+
+
 def test_oriented_weight_takes_no_backward_vertices(oracle_mod):
     """On an orientation a k-clique's first vertex needs k - 1 out-neighbours, so the
     step-1 weight is binom(d+, k - 1) times the other factors; a vertex with fewer
@@ -135,12 +150,13 @@ def test_oriented_trials_bit_exact(agis, oracle_mod, oriented, gname, name):
     k, edges = I.PATTERNS[name]
     p = agis.Pattern(k, edges)
     for mode in (0, 1, 2):
-        emb, hit, x, sec = agis.dump_trials(o, p, agis.default_opts(mode=mode, seed=9), 1000, 2100)
-        q = oracle_mod.Query(oo, oc, k, edges, nsum=nsum, hits=hits, c_min=CMIN, mode=mode, seed=9,
-                             oriented=True)
-        oemb, ohit, ox, osec = q.trials(1000, 2100)
-        bad = np.nonzero((emb != oemb).any(axis=1) | (hit != ohit) | (x != ox) | (sec != osec))[0]
-        assert len(bad) == 0, (name, mode, int(bad[0]))
+        for anchor in (0, 1):
+            emb, hit, x, sec = agis.dump_trials(o, p, agis.default_opts(mode=mode, seed=9, anchor=anchor), 1000, 2100)
+            q = oracle_mod.Query(oo, oc, k, edges, nsum=nsum, hits=hits, c_min=CMIN, mode=mode, seed=9,
+                                 oriented=True, anchor=bool(anchor))
+            oemb, ohit, ox, osec = q.trials(1000, 2100)
+            bad = np.nonzero((emb != oemb).any(axis=1) | (hit != ohit) | (x != ox) | (sec != osec))[0]
+            assert len(bad) == 0, (name, mode, anchor, int(bad[0]))
 
 
 @pytest.mark.gpu
