@@ -989,26 +989,18 @@ int launch_sampler(agis_graph *g, LaunchBuffers &lb, int grid, const DumpView *d
 int add_sampler_node(agis_graph *g, LaunchBuffers &lb, int grid, cudaGraph_t graph,
                      const cudaGraphNode_t *deps, size_t ndeps, cudaGraphNode_t *node, bool anchor)
 {
-    static GraphView gv;
-    static DumpView none;
-    static const DevQuery *q;
-    static const WorkItem *it;
-    static const uint32_t *nptr;
-    static uint32_t *ctr;
-    static uint64_t *out;
-    static uint64_t z0, z1;
-    static char *scr;
-    static uint32_t cap;
-    gv = GraphView{g->off, g->cols, g->nv, g->nnz, g->hub_id, g->hub_bits, g->hub_words, g->rp_base};
-    none = DumpView{nullptr, nullptr, nullptr, nullptr, 0};
-    q = lb.d_queries;
-    it = lb.d_items;
-    nptr = lb.d_counter + 1;
-    ctr = lb.d_counter;
-    out = lb.d_out;
-    z0 = z1 = 0;
-    scr = (char *)lb.d_scratch;
-    cap = lb.scratch_cap;
+    // the argument values are copied into the node when it is added, so locals do
+    // (and concurrent servers on different graphs share nothing here)
+    GraphView gv{g->off, g->cols, g->nv, g->nnz, g->hub_id, g->hub_bits, g->hub_words, g->rp_base};
+    DumpView none{nullptr, nullptr, nullptr, nullptr, 0};
+    const DevQuery *q = lb.d_queries;
+    const WorkItem *it = lb.d_items;
+    const uint32_t *nptr = lb.d_counter + 1;
+    uint32_t *ctr = lb.d_counter;
+    uint64_t *out = lb.d_out;
+    uint64_t z0 = 0, z1 = 0;
+    char *scr = (char *)lb.d_scratch;
+    uint32_t cap = lb.scratch_cap;
     void *args[] = {&gv, &q, &it, &nptr, &ctr, &out, &none, &z0, &z1, &scr, &cap};
     cudaKernelNodeParams p = {};
     p.func = anchor ? (void *)sample_kernel<false, true> : (void *)sample_kernel<false, false>;
