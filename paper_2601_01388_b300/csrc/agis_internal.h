@@ -192,7 +192,10 @@ size_t table_bytes(const agis_graph *g, const int32_t cfg[4], bool need_pref, bo
 void free_table(WeightTable &t);
 
 // sample.cu
-// anchor: some staged query uses the anchor draw (selects the kernel instance)
+// sample.cu: the kernel instance for dumps, or for launches with (anchor) or
+// without anchor-draw queries
+const void *sampler_function(bool dump, bool anchor);
+// launch.cu.  anchor: some staged query uses the anchor draw (selects the instance)
 int launch_sampler(agis_graph *g, LaunchBuffers &lb, int grid, const DumpView *dump,
                    cudaStream_t stream, uint64_t implicit_first, uint64_t implicit_count,
                    uint64_t *tile_out, bool anchor);

@@ -960,55 +960,12 @@ int sampler_occupancy(int *blocks_per_sm)
                                                                     kBlock, 0));
 }
 
-// Enqueue one sampler launch over lb's staged queries and items (already on the
-// device; lb.d_counter[0] zeroed and lb.d_counter[1] = number of items).  With
-// implicit_count > 0 the items are implicit tiles of query 0 (see the kernel).
-int launch_sampler(agis_graph *g, LaunchBuffers &lb, int grid, const DumpView *dump,
-                   cudaStream_t stream, uint64_t implicit_first, uint64_t implicit_count,
-                   uint64_t *tile_out, bool anchor)
+// The kernel instances, for the launch code in launch.cu: the dump instance, the
+// anchor-capable one, and the plain one.
+const void *sampler_function(bool dump, bool anchor)
 {
-    GraphView gv{g->off, g->cols, g->nv, g->nnz, g->hub_id, g->hub_bits, g->hub_words, g->rp_base};
-    const WorkItem *items = implicit_count ? nullptr : lb.d_items;
-    uint64_t *out = tile_out ? tile_out : lb.d_out;
-    if (dump) {
-        count_launch();
-        sample_kernel<true, true><<<grid, kBlock, 0, stream>>>(gv, lb.d_queries, items, lb.d_counter + 1,
-                                                               lb.d_counter, out, *dump, implicit_first,
-                                                               implicit_count, (char *)lb.d_scratch, lb.scratch_cap);
-    } else {
-        DumpView none{nullptr, nullptr, nullptr, nullptr, 0};
-        count_launch();
-        auto *kern = anchor ? sample_kernel<false, true> : sample_kernel<false, false>;
-        kern<<<grid, kBlock, 0, stream>>>(gv, lb.d_queries, items, lb.d_counter + 1, lb.d_counter, out, none,
-                                          implicit_first, implicit_count, (char *)lb.d_scratch, lb.scratch_cap);
-    }
-    return cuda_status(cudaGetLastError());
-}
-
-// Adds the sampler as a kernel node of a CUDA graph (explicit items, no dump).
-int add_sampler_node(agis_graph *g, LaunchBuffers &lb, int grid, cudaGraph_t graph,
-                     const cudaGraphNode_t *deps, size_t ndeps, cudaGraphNode_t *node, bool anchor)
-{
-    // the argument values are copied into the node when it is added, so locals do
-    // (and concurrent servers on different graphs share nothing here)
-    GraphView gv{g->off, g->cols, g->nv, g->nnz, g->hub_id, g->hub_bits, g->hub_words, g->rp_base};
-    DumpView none{nullptr, nullptr, nullptr, nullptr, 0};
-    const DevQuery *q = lb.d_queries;
-    const WorkItem *it = lb.d_items;
-    const uint32_t *nptr = lb.d_counter + 1;
-    uint32_t *ctr = lb.d_counter;
-    uint64_t *out = lb.d_out;
-    uint64_t z0 = 0, z1 = 0;
-    char *scr = (char *)lb.d_scratch;
-    uint32_t cap = lb.scratch_cap;
-    void *args[] = {&gv, &q, &it, &nptr, &ctr, &out, &none, &z0, &z1, &scr, &cap};
-    cudaKernelNodeParams p = {};
-    p.func = anchor ? (void *)sample_kernel<false, true> : (void *)sample_kernel<false, false>;
-    p.gridDim = dim3(grid);
-    p.blockDim = dim3(kBlock);
-    p.sharedMemBytes = 0;
-    p.kernelParams = args;
-    return cuda_status(cudaGraphAddKernelNode(node, graph, deps, ndeps, &p));
+    if (dump) return (const void *)sample_kernel<true, true>;
+    return anchor ? (const void *)sample_kernel<false, true> : (const void *)sample_kernel<false, false>;
 }
 
 }  // namespace agis
