@@ -64,7 +64,8 @@ def parse_args():
                          "device; 6-clique and 7-cycle to +-1%% under f_approx and f_uniform (2^30-trial budget)")
     ap.add_argument("--large-scale", type=int, default=28)
     ap.add_argument("--serve", action="store_true",
-                    help="also run the serving load (saturation, then Poisson at 50/80/95%%)")
+                    help="also run the serving configuration: Chung-Lu n=10M and R-MAT scale 24 resident on the "
+                         "device, serving load on each (saturation, then Poisson at 50/80/95%%)")
     ap.add_argument("--serve-seconds", type=float, default=15.0)
     ap.add_argument("--concentration", action="store_true",
                     help="also run the concentration workload: all 6 four-vertex and 21 five-vertex "
@@ -365,6 +366,33 @@ def serve_load(agis, g, seconds, seed=7, max_slots=64, budget=200 << 30, burst=6
     srv.close()
     out["epochs"] = st["epochs"]
     out["peak_slots"] = st["peak_slots"]
+    return out
+
+
+def serving_configs(agis, ctx, seconds):
+    """The serving configuration: a Chung-Lu power-law graph (10M vertices, degree
+    exponent 2.1, mean degree 32) and the scale-24 R-MAT, both generated on the
+    device and resident together; the serving load runs against each in turn."""
+    import torch
+    graphs = []
+    t0 = time.perf_counter()
+    cl = agis.Graph.chung_lu(ctx, 10_000_000, 2.1, 32.0, seed=1)
+    cl.preprocess(1, CMIN)
+    graphs.append(("Chung-Lu n=10M gamma=2.1 mean degree 32", cl, time.perf_counter() - t0))
+    t0 = time.perf_counter()
+    rm = agis.Graph.rmat(ctx, 24, 16, 0.57, 0.19, 0.19, seed=1)
+    rm.preprocess(1, CMIN)
+    graphs.append(("R-MAT scale 24 edge factor 16", rm, time.perf_counter() - t0))
+    out = []
+    for label, g, t_build in graphs:
+        info = g.info()
+        r = serve_load(agis, g, seconds)
+        r.update({"graph": label, "nv": info["nv"], "nnz": info["nnz"], "max_degree": info["max_degree"],
+                  "build_and_preprocess_s": t_build})
+        out.append(r)
+    for _, g, _ in graphs:
+        g.close()
+    torch.cuda.empty_cache()
     return out
 
 
@@ -789,7 +817,7 @@ def run_gpu(args, world, rank, local):
 
         serving = None
         if args.serve:
-            serving = serve_load(agis, g, args.serve_seconds)
+            serving = serving_configs(agis, ctx, args.serve_seconds)
 
         abl = None
         if args.ablation:
