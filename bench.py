@@ -402,7 +402,8 @@ def batch64(agis, ctx, scale, stream):
     """64 pattern queries (cliques, cycles, paths, stars of 3-7 vertices, tailed
     triangle, diamond, chordal 5-cycle) with fixed trial budgets log-uniform in
     2^16..2^26 on an R-MAT graph generated on the device: all of them in one
-    persistent launch (after the grid autotuner) against 64 plain launches."""
+    persistent launch (after the autotuner picks CTAs per SM and tiles per item)
+    against 64 plain launches."""
     import torch
     from paper_2601_01388_b300 import inputs as I
     t0 = time.perf_counter()
@@ -418,7 +419,7 @@ def batch64(agis, ctx, scale, stream):
     for p, o in zip(pats, opts):
         agis.prepare(g, p, o)
     t_tables = time.perf_counter() - t0
-    best = agis.autotune(g, pats, opts, 1 << 15)
+    best, span = agis.autotune(g, pats, opts, 1 << 15)
     total = sum(b for _, _, b in qs)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -432,7 +433,7 @@ def batch64(agis, ctx, scale, stream):
     g.close()
     return {"graph": f"R-MAT scale {scale} (device), nv {info['nv']}, nnz {info['nnz']}, max degree {info['max_degree']}",
             "generate_s": t_gen, "preprocess_s": t_prep, "tables_s": t_tables, "queries": len(qs),
-            "trials": total, "autotuned_ctas_per_sm": best, "plain_s": t_plain, "batched_s": t_batch,
+            "trials": total, "autotuned_ctas_per_sm": best, "autotuned_tiles_per_item": span, "plain_s": t_plain, "batched_s": t_batch,
             "plain_samples_per_s": total / t_plain, "batched_samples_per_s": total / t_batch,
             "same_results": same}
 

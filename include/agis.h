@@ -273,14 +273,17 @@ int agis_tile_trials(void);
 int agis_sample_device(agis_graph *g, const agis_pattern *p, const agis_opts *opts,
                        uint64_t first, uint64_t ntiles, uint64_t *tile_out);
 
-/* agis_autotune: picks the sampler's persistent grid for this graph and query mix
- * -- resident CTAs per SM, 1 up to the occupancy limit -- by timing a fixed budget
- * of trials_per_query trials of every query at each setting (CUDA events on the
+/* agis_autotune: picks the sampler's launch shape for this graph and query mix --
+ * resident CTAs per SM (1 up to the occupancy limit) and tiles per work item (1, 2
+ * or 4 tiles of agis_tile_trials() trials each) -- by timing a fixed budget of
+ * trials_per_query trials of every query at each pair (CUDA events on the
  * context's stream), and keeps the fastest in the context for later launches.
- * Results never depend on the setting (tiles and their sums are fixed).
- * *blocks_per_sm (may be NULL) receives the choice.  Errors: ARG, STATE, NOMEM, CUDA. */
+ * Short epochs still split into single tiles so that every SM gets work.  Results
+ * never depend on the choice: tiles and their fixed-order sums stay the same.
+ * *blocks_per_sm and *tiles_per_item (either may be NULL) receive the choice.
+ * Errors: ARG, STATE, NOMEM, CUDA. */
 int agis_autotune(agis_graph *g, int n, const agis_pattern *const *patterns, const agis_opts *opts,
-                  uint64_t trials_per_query, int32_t *blocks_per_sm);
+                  uint64_t trials_per_query, int32_t *blocks_per_sm, int32_t *tiles_per_item);
 
 /* agis_prepare: builds, for the query's f_approx steps, the quantised weight tables
  * of Eq. probability_function and their prefix sums (Sec. 4.4 / Sec. 5.1: f_approx

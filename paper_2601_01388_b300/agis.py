@@ -85,7 +85,7 @@ _sig = {
     "agis_dump_trials": ([VP, VP, P(Opts), C.c_uint64, C.c_uint64, VP, VP, VP, VP], C.c_int),
     "agis_sample_device": ([VP, VP, P(Opts), C.c_uint64, C.c_uint64, VP], C.c_int),
     "agis_prepare": ([VP, VP, P(Opts)], C.c_int),
-    "agis_autotune": ([VP, C.c_int, P(VP), P(Opts), C.c_uint64, P(C.c_int32)], C.c_int),
+    "agis_autotune": ([VP, C.c_int, P(VP), P(Opts), C.c_uint64, P(C.c_int32), P(C.c_int32)], C.c_int),
     "agis_z_of_delta": ([C.c_double], C.c_double),
     "agis_tile_trials": ([], C.c_int),
     "agis_kernel_launches": ([], C.c_uint64),
@@ -378,13 +378,15 @@ def dump_trials(graph: Graph, pattern: Pattern, opts: Opts, first: int, count: i
     return emb, hit, x, sec
 
 
-def autotune(graph: Graph, patterns, opts_list, trials_per_query=1 << 16) -> int:
+def autotune(graph: Graph, patterns, opts_list, trials_per_query=1 << 16):
+    """Returns the chosen (CTAs per SM, tiles per work item)."""
     n = len(patterns)
     ph = (VP * n)(*[p.h for p in patterns])
     oa = (Opts * n)(*opts_list)
     b = C.c_int32()
-    _check(_lib.agis_autotune(graph.h, n, ph, oa, trials_per_query, C.byref(b)), "agis_autotune")
-    return b.value
+    t = C.c_int32()
+    _check(_lib.agis_autotune(graph.h, n, ph, oa, trials_per_query, C.byref(b), C.byref(t)), "agis_autotune")
+    return b.value, t.value
 
 
 def prepare(graph: Graph, pattern: Pattern, opts: Opts):

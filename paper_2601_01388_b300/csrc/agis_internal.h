@@ -24,6 +24,9 @@ constexpr int kMaxK = 8;
 #endif
 constexpr int kTile = AGIS_TILE;     // trials per work item (one CTA at a time)
 static_assert(kTile >= 32 && kTile <= 1024 && (kTile & (kTile - 1)) == 0, "tile: power of two in [32, 1024]");
+// A work item covers 1..kMaxSpan consecutive tiles of one query; each tile keeps its
+// own fixed-order reduction and output slot, so results never depend on the span.
+constexpr int kMaxSpan = 4;
 constexpr int kBlock = 256;          // threads per CTA of the sampler
 constexpr int kWarps = kBlock / 32;
 constexpr uint64_t kStreamTrial = 1; // Philox counter word 2 of a trial draw
@@ -51,8 +54,9 @@ struct DevQuery {
     DevStep step[kMaxK];
 };
 
-// A work item: `count` trials of query `query` starting at trial `first`; the tile
-// sums go to out[4*slot .. 4*slot+3] (hits, sectors, bits of sum X, bits of sum X^2).
+// A work item: `count` trials (at most kMaxSpan tiles) of query `query` starting at
+// trial `first`; the sums of its t-th tile go to out[4*(slot+t) .. 4*(slot+t)+3]
+// (hits, sectors, bits of sum X, bits of sum X^2).
 struct WorkItem {
     uint32_t query;
     uint32_t count;
@@ -133,6 +137,7 @@ struct agis_ctx {
     bool own_stream = false;
     int sm_count = 0;
     int blocks_per_sm = 0;      // sampler CTAs per SM chosen by the autotuner (0 = not tuned)
+    int span = 0;               // tiles per work item chosen by the autotuner (0 = not tuned)
 };
 
 struct agis_pattern {

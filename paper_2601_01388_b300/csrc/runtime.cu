@@ -324,25 +324,37 @@ void fill_result(const QueryRun &r, agis_result *out)
     out->t_prep_s = r.t_prep;
 }
 
-// Stages items for the given runs (tile ranges) into lb's pinned buffers.
-size_t stage_items(LaunchBuffers &lb, std::vector<QueryRun *> &runs, const std::vector<uint64_t> &ntiles)
+// Tiles per work item for an epoch of `tiles` tiles on `grid` CTAs: the autotuned
+// span (else kMaxSpan), halved while the CTAs would get fewer than two items each,
+// so that short epochs (a query's first checkpoint) still spread over every SM.
+int span_for(const agis_graph *g, size_t tiles, int grid)
 {
-    size_t k = 0;
+    int span = g->ctx->span > 0 ? g->ctx->span : kMaxSpan;
+    while (span > 1 && tiles < (size_t)span * (size_t)grid * 2) span >>= 1;
+    return span;
+}
+
+// Stages items of up to `span` tiles for the given runs (tile ranges) into lb's
+// pinned buffers; tile output slots run 0, 1, ... in query then tile order.
+// Returns the number of items.
+size_t stage_items(LaunchBuffers &lb, std::vector<QueryRun *> &runs, const std::vector<uint64_t> &ntiles, int span)
+{
+    size_t k = 0, m = 0;
     for (size_t q = 0; q < runs.size(); ++q) {
         const QueryRun &r = *runs[q];
         lb.h_queries[q] = r.dq;
-        for (uint64_t j = 0; j < ntiles[q]; ++j) {
-            const uint64_t tile = r.done_tiles + j;
-            const uint64_t first = tile * kTile;
-            WorkItem &w = lb.h_items[k];
+        for (uint64_t j = 0; j < ntiles[q]; j += (uint64_t)span) {
+            const uint64_t nt = std::min<uint64_t>((uint64_t)span, ntiles[q] - j);
+            const uint64_t first = (r.done_tiles + j) * kTile;
+            WorkItem &w = lb.h_items[m++];
             w.query = (uint32_t)q;
-            w.count = (uint32_t)std::min<uint64_t>(kTile, r.o.max_trials - first);
+            w.count = (uint32_t)std::min<uint64_t>(nt * kTile, r.o.max_trials - first);
             w.first = first;
             w.slot = k;
-            ++k;
+            k += nt;
         }
     }
-    return k;
+    return m;
 }
 
 // One epoch by plain stream launches.
@@ -360,7 +372,7 @@ int run_epoch_direct(agis_graph *g, std::vector<QueryRun *> &runs, const std::ve
     cudaStream_t st = g->ctx->stream;
     int rc = ensure_buffers(lb, runs.size(), total);
     if (rc != AGIS_OK) return rc;
-    const size_t n = stage_items(lb, runs, ntiles);
+    const size_t n = stage_items(lb, runs, ntiles, span_for(g, total, grid_for(g, total)));
     lb.h_counter[0] = 0;
     lb.h_counter[1] = (uint32_t)n;
     AGIS_CUDA_TRY(cudaMemcpyAsync(lb.d_queries, lb.h_queries, sizeof(DevQuery) * runs.size(), cudaMemcpyHostToDevice, st));
@@ -370,7 +382,7 @@ int run_epoch_direct(agis_graph *g, std::vector<QueryRun *> &runs, const std::ve
     if ((rc = ensure_scratch(g, lb, grid)) != AGIS_OK) return rc;
     rc = launch_sampler(g, lb, grid, nullptr, st, 0, 0, nullptr, any_anchor(runs));
     if (rc != AGIS_OK) return rc;
-    AGIS_CUDA_TRY(cudaMemcpyAsync(lb.h_out, lb.d_out, sizeof(uint64_t) * 4 * n, cudaMemcpyDeviceToHost, st));
+    AGIS_CUDA_TRY(cudaMemcpyAsync(lb.h_out, lb.d_out, sizeof(uint64_t) * 4 * total, cudaMemcpyDeviceToHost, st));
     AGIS_CUDA_TRY(cudaStreamSynchronize(st));
     return AGIS_OK;
 }
@@ -385,10 +397,10 @@ int run_epoch_graph(agis_graph *g, std::vector<QueryRun *> &runs, const std::vec
     cudaStream_t st = g->ctx->stream;
     int rc = ensure_buffers(lb, runs.size(), total);
     if (rc != AGIS_OK) return rc;
-    const size_t n = stage_items(lb, runs, ntiles);
+    const int grid = grid_for(g, (size_t)g->ctx->sm_count * 64);
+    const size_t n = stage_items(lb, runs, ntiles, span_for(g, total, grid));
     lb.h_counter[0] = 0;
     lb.h_counter[1] = (uint32_t)n;
-    const int grid = grid_for(g, (size_t)g->ctx->sm_count * 64);
     if ((rc = ensure_scratch(g, lb, grid)) != AGIS_OK) return rc;
     const bool anchor = any_anchor(runs);
     if (!lb.exec || lb.graph_generation != lb.generation || lb.graph_grid != grid || lb.graph_anchor != anchor) {
@@ -417,7 +429,8 @@ int run_epoch_graph(agis_graph *g, std::vector<QueryRun *> &runs, const std::vec
     AGIS_CUDA_TRY(cudaGraphExecMemcpyNodeSetParams1D(lb.exec, lb.n_h2d_i, lb.d_items, lb.h_items,
                                                      sizeof(WorkItem) * std::max<size_t>(n, 1), cudaMemcpyHostToDevice));
     AGIS_CUDA_TRY(cudaGraphExecMemcpyNodeSetParams1D(lb.exec, lb.n_d2h, lb.h_out, lb.d_out,
-                                                     sizeof(uint64_t) * 4 * std::max<size_t>(n, 1), cudaMemcpyDeviceToHost));
+                                                     sizeof(uint64_t) * 4 * std::max<size_t>(total, 1),
+                                                     cudaMemcpyDeviceToHost));
     count_launch();
     AGIS_CUDA_TRY(cudaGraphLaunch(lb.exec, st));
     AGIS_CUDA_TRY(cudaStreamSynchronize(st));
@@ -733,7 +746,7 @@ extern "C" int agis_prepare(agis_graph *g, const agis_pattern *p, const agis_opt
 extern "C" uint64_t agis_kernel_launches(void) { return g_launches.load(); }
 
 extern "C" int agis_autotune(agis_graph *g, int n, const agis_pattern *const *patterns, const agis_opts *opts,
-                             uint64_t trials_per_query, int32_t *blocks_per_sm)
+                             uint64_t trials_per_query, int32_t *blocks_per_sm, int32_t *tiles_per_item)
 {
     if (!g || n <= 0 || !patterns || !opts || trials_per_query == 0) return AGIS_ERR_ARG;
     std::lock_guard<std::recursive_mutex> lk(g->mu);
@@ -742,6 +755,7 @@ extern "C" int agis_autotune(agis_graph *g, int n, const agis_pattern *const *pa
     int occ = 1;
     int rc = sampler_occupancy(&occ);
     if (rc != AGIS_OK) return rc;
+    occ = std::max(1, occ);
     const uint64_t ntiles = (trials_per_query + kTile - 1) / kTile;
     std::vector<DevQuery> dqs((size_t)n);
     bool anchor = false;
@@ -751,50 +765,55 @@ extern "C" int agis_autotune(agis_graph *g, int n, const agis_pattern *const *pa
         anchor = anchor || (dqs[(size_t)i].flags & kFlagAnchor);
     }
     LaunchBuffers &lb = g->lb;
-    const size_t items = (size_t)n * ntiles;
-    if ((rc = ensure_buffers(lb, (size_t)n, items)) != AGIS_OK) return rc;
-    if ((rc = ensure_scratch(g, lb, g->ctx->sm_count * std::max(1, occ))) != AGIS_OK) return rc;
+    const size_t tiles = (size_t)n * ntiles;
+    if ((rc = ensure_buffers(lb, (size_t)n, tiles)) != AGIS_OK) return rc;
+    if ((rc = ensure_scratch(g, lb, g->ctx->sm_count * occ)) != AGIS_OK) return rc;
     AGIS_CUDA_TRY(cudaStreamSynchronize(st));
-    size_t k = 0;
-    for (int i = 0; i < n; ++i) {
-        lb.h_queries[i] = dqs[(size_t)i];
-        for (uint64_t j = 0; j < ntiles; ++j, ++k) {
-            WorkItem &w = lb.h_items[k];
-            w.query = (uint32_t)i;
-            w.count = kTile;
-            w.first = j * kTile;
-            w.slot = k;
-        }
-    }
+    for (int i = 0; i < n; ++i) lb.h_queries[i] = dqs[(size_t)i];
     AGIS_CUDA_TRY(cudaMemcpyAsync(lb.d_queries, lb.h_queries, sizeof(DevQuery) * (size_t)n, cudaMemcpyHostToDevice, st));
-    AGIS_CUDA_TRY(cudaMemcpyAsync(lb.d_items, lb.h_items, sizeof(WorkItem) * items, cudaMemcpyHostToDevice, st));
     cudaEvent_t e0, e1;
     AGIS_CUDA_TRY(cudaEventCreate(&e0));
     AGIS_CUDA_TRY(cudaEventCreate(&e1));
-    int best = 1;
-    float best_ms = 0.0f;
-    for (int c = 1; c <= std::max(1, occ); ++c) {
-        const int grid = (int)std::min<size_t>((size_t)g->ctx->sm_count * (size_t)c, items);
-        float ms_total = 0.0f;
-        for (int rep = 0; rep < 2; ++rep) {          // the first launch warms caches
-            const uint32_t counter[2] = {0u, (uint32_t)items};
-            cudaMemcpyAsync(lb.d_counter, counter, sizeof(counter), cudaMemcpyHostToDevice, st);
-            cudaEventRecord(e0, st);
-            rc = launch_sampler(g, lb, grid, nullptr, st, 0, 0, nullptr, anchor);
-            cudaEventRecord(e1, st);
-            if (rc != AGIS_OK) break;
-            if (cudaEventSynchronize(e1) != cudaSuccess) { rc = AGIS_ERR_CUDA; break; }
-            float ms = 0.0f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (rep == 1) ms_total = ms;
+    // every (CTAs per SM, tiles per item) pair on the same trials; the first launch
+    // only warms the caches
+    int best_c = occ, best_s = 1;
+    float best_ms = -1.0f;
+    for (int trial = -1; trial < occ * 3 && rc == AGIS_OK; ++trial) {
+        const int c = trial < 0 ? occ : 1 + trial / 3;
+        const int span = trial < 0 ? 1 : 1 << (trial % 3);
+        size_t m = 0;
+        for (int i = 0; i < n; ++i) {
+            for (uint64_t j = 0; j < ntiles; j += (uint64_t)span) {
+                WorkItem &w = lb.h_items[m++];
+                w.query = (uint32_t)i;
+                w.count = (uint32_t)(std::min<uint64_t>((uint64_t)span, ntiles - j) * kTile);
+                w.first = j * kTile;
+                w.slot = (uint64_t)i * ntiles + j;
+            }
         }
+        const uint32_t counter[2] = {0u, (uint32_t)m};
+        cudaMemcpyAsync(lb.d_items, lb.h_items, sizeof(WorkItem) * m, cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(lb.d_counter, counter, sizeof(counter), cudaMemcpyHostToDevice, st);
+        const int grid = (int)std::min<size_t>((size_t)g->ctx->sm_count * (size_t)c, m);
+        cudaEventRecord(e0, st);
+        rc = launch_sampler(g, lb, grid, nullptr, st, 0, 0, nullptr, anchor);
+        cudaEventRecord(e1, st);
         if (rc != AGIS_OK) break;
-        if (c == 1 || ms_total < best_ms) { best_ms = ms_total; best = c; }
+        if (cudaEventSynchronize(e1) != cudaSuccess) { rc = AGIS_ERR_CUDA; break; }
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (trial >= 0 && (best_ms < 0.0f || ms < best_ms)) {
+            best_ms = ms;
+            best_c = c;
+            best_s = span;
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc != AGIS_OK) return rc;
-    g->ctx->blocks_per_sm = best;
-    if (blocks_per_sm) *blocks_per_sm = best;
+    g->ctx->blocks_per_sm = best_c;
+    g->ctx->span = best_s;
+    if (blocks_per_sm) *blocks_per_sm = best_c;
+    if (tiles_per_item) *tiles_per_item = best_s;
     return AGIS_OK;
 }

@@ -835,13 +835,13 @@ __global__ void __launch_bounds__(kBlock, AGIS_MIN_BLOCKS) sample_kernel(GraphVi
                                                         uint32_t scratch_cap)
 {
     __shared__ DevQuery sq;
-    __shared__ double xs[kTile];
+    __shared__ double xs[kMaxSpan * kTile];
     __shared__ double red[kBlock];
     __shared__ double red2[kBlock];
     __shared__ int32_t tau_s[kWarps][kMaxK];
     __shared__ uint64_t s_top[kTopSplitters];
-    __shared__ uint32_t s_item, s_next, s_hits;
-    __shared__ unsigned long long s_sec;
+    __shared__ uint32_t s_item, s_next, s_hits[kMaxSpan];
+    __shared__ unsigned long long s_sec[kMaxSpan];
     __shared__ int s_query, s_reload;
     __shared__ WorkItem s_it;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -879,8 +879,10 @@ __global__ void __launch_bounds__(kBlock, AGIS_MIN_BLOCKS) sample_kernel(GraphVi
                 s_query = (int)w.query;
             }
             s_next = 0;
-            s_hits = 0;
-            s_sec = 0;
+            for (int t = 0; t < kMaxSpan; ++t) {
+                s_hits[t] = 0;
+                s_sec[t] = 0;
+            }
         }
         __syncthreads();
         if (s_item >= n_items) break;
@@ -898,7 +900,8 @@ __global__ void __launch_bounds__(kBlock, AGIS_MIN_BLOCKS) sample_kernel(GraphVi
                 s_top[k] = pos >= 0 ? __ldg(P + pos) : 0;
             }
         }
-        for (int j = threadIdx.x; j < kTile; j += kBlock) xs[j] = 0.0;
+        const int ntile = (int)((it.count + kTile - 1) / kTile);
+        for (int j = threadIdx.x; j < ntile * kTile; j += kBlock) xs[j] = 0.0;
         __syncthreads();
         for (;;) {
             uint32_t tt = 0;
@@ -909,8 +912,8 @@ __global__ void __launch_bounds__(kBlock, AGIS_MIN_BLOCKS) sample_kernel(GraphVi
             const TrialOut r = run_trial<kAnchor>(g, sq, t, tau_s[warp], ws, s_top, lane);
             if (lane == 0) {
                 xs[tt] = r.x;
-                if (r.hit) atomicAdd(&s_hits, 1u);
-                atomicAdd(&s_sec, (unsigned long long)r.sectors);
+                if (r.hit) atomicAdd(&s_hits[tt / kTile], 1u);
+                atomicAdd(&s_sec[tt / kTile], (unsigned long long)r.sectors);
                 if (kDump) {
                     const uint64_t d = t - dump.first;
                     if (dump.hit) dump.hit[d] = (uint8_t)r.hit;
@@ -922,33 +925,35 @@ __global__ void __launch_bounds__(kBlock, AGIS_MIN_BLOCKS) sample_kernel(GraphVi
             __syncwarp();
         }
         __syncthreads();
-        // fixed-order reduction of the tile: strided partial sums, then a tree
-        {
-            double s = 0.0, s2 = 0.0;
-            for (int j = threadIdx.x; j < kTile; j += kBlock) {
-                const double x = xs[j];
-                s += x;
-                s2 += x * x;
+        // fixed-order reduction of each tile: strided partial sums, then a tree
+        for (int tl = 0; tl < ntile; ++tl) {
+            {
+                double s = 0.0, s2 = 0.0;
+                for (int j = threadIdx.x; j < kTile; j += kBlock) {
+                    const double x = xs[tl * kTile + j];
+                    s += x;
+                    s2 += x * x;
+                }
+                red[threadIdx.x] = s;
+                red2[threadIdx.x] = s2;
             }
-            red[threadIdx.x] = s;
-            red2[threadIdx.x] = s2;
-        }
-        __syncthreads();
-        for (int w = kBlock / 2; w > 0; w >>= 1) {
-            if (threadIdx.x < w) {
-                red[threadIdx.x] += red[threadIdx.x + w];
-                red2[threadIdx.x] += red2[threadIdx.x + w];
+            __syncthreads();
+            for (int w = kBlock / 2; w > 0; w >>= 1) {
+                if (threadIdx.x < w) {
+                    red[threadIdx.x] += red[threadIdx.x + w];
+                    red2[threadIdx.x] += red2[threadIdx.x + w];
+                }
+                __syncthreads();
+            }
+            if (threadIdx.x == 0) {
+                uint64_t *o = tile_out + 4 * ((uint64_t)it.slot + tl);
+                o[0] = s_hits[tl];
+                o[1] = s_sec[tl];
+                o[2] = (uint64_t)__double_as_longlong(red[0]);
+                o[3] = (uint64_t)__double_as_longlong(red2[0]);
             }
             __syncthreads();
         }
-        if (threadIdx.x == 0) {
-            uint64_t *o = tile_out + 4 * it.slot;
-            o[0] = s_hits;
-            o[1] = s_sec;
-            o[2] = (uint64_t)__double_as_longlong(red[0]);
-            o[3] = (uint64_t)__double_as_longlong(red2[0]);
-        }
-        __syncthreads();
     }
 }
 

@@ -1,4 +1,5 @@
-"""The grid autotuner (results must not depend on the grid it picks) and the
+"""The launch autotuner (results must not depend on the grid or the tiles per item
+it picks) and the
 random-access read probe."""
 import numpy as np
 import pytest
@@ -27,11 +28,13 @@ def test_autotune_keeps_results(agis):
     pats = [agis.Pattern(*I.PATTERNS[n]) for n in ("4-clique", "house", "5-cycle")]
     opts = [agis.default_opts(mode=m, seed=3 + m, eps=0.0, max_trials=50000) for m in range(3)]
     before = [agis.estimate(g, p, o) for p, o in zip(pats, opts)]
-    best = agis.autotune(g, pats, opts, 1 << 15)
-    assert best >= 1
+    best, span = agis.autotune(g, pats, opts, 1 << 15)
+    assert best >= 1 and span in (1, 2, 4)
     after = [agis.estimate(g, p, o) for p, o in zip(pats, opts)]
-    for a, b in zip(before, after):
-        assert a["sum_x"] == b["sum_x"] and a["hits"] == b["hits"] and a["sectors"] == b["sectors"]
+    batched = agis.estimate_batch(g, pats, opts)
+    for a, b, c in zip(before, after, batched):
+        assert a["sum_x"] == b["sum_x"] == c["sum_x"] and a["hits"] == b["hits"] == c["hits"]
+        assert a["sectors"] == b["sectors"] == c["sectors"]
 
 
 def test_random_read_probe_runs(agis):
@@ -43,3 +46,28 @@ def test_random_read_probe_runs(agis):
     assert int(sink.item()) == 0          # all-zero buffer: the xor never hits the marker
     with pytest.raises(agis.AgisError):
         agis.probe_random_read(buf.data_ptr(), 100, 1, 1, 0, sink.data_ptr())
+
+
+def test_multi_tile_items_keep_tile_sums(agis):
+    """2^21 trials in one epoch run as items of several tiles; summing the per-tile
+    outputs of single-tile items (sample_device) in order gives the same totals."""
+    import torch
+    ctx = agis.Context(0)
+    off, cols = I.rmat_graph(13, 16, seed=6)
+    g = agis.Graph(ctx, off, cols)
+    g.preprocess(1, 2.0 ** -10)
+    p = agis.Pattern(*I.PATTERNS["house"])
+    n = 1 << 21
+    for mode in (0, 2):
+        o = agis.default_opts(mode=mode, seed=12, eps=0.0, max_trials=n, chunk_trials=n)
+        r = agis.estimate(g, p, o)
+        ntiles = n // agis.TILE
+        out = torch.zeros(ntiles * 4, dtype=torch.int64, device="cuda")
+        agis.sample_device(g, p, o, 0, ntiles, out.data_ptr())
+        torch.cuda.synchronize()
+        h, sec, sx, sx2 = agis.tile_sums(out.cpu().numpy().view(np.uint64))
+        acc = 0.0
+        for v in sx:
+            acc += float(v)
+        assert r["trials"] == n and r["hits"] == int(h.sum()) and r["sectors"] == int(sec.sum())
+        assert r["sum_x"] == acc
