@@ -163,3 +163,38 @@ def test_device_chung_lu_is_a_valid_power_law_graph(agis):
     g2 = agis.Graph.chung_lu(ctx, n, 2.1, 32.0, seed=3)
     o2, c2 = g2.csr()
     assert (o2 == off).all() and (c2 == cols).all()
+
+
+def test_two_servers_on_two_graphs_concurrently(agis, setup):
+    """Two servers (two scheduler threads, each building and replaying its own CUDA
+    graph) on two resident graphs at once, with anchor-draw and term-mask queries
+    in the mix: every result equals the same query run alone."""
+    ctx, g = setup
+    off2, cols2 = I.rmat_graph(11, 16, seed=9)
+    g2 = agis.Graph(ctx, off2, cols2)
+    g2.preprocess(1, CMIN)
+    qs = queries(agis, 8)
+    extra = agis.default_opts(seed=77, anchor=1, terms=3, eps=0.03, chunk_trials=4096, min_trials=4096,
+                              max_trials=1 << 21)
+    qs.append((agis.Pattern(*I.PATTERNS["house"]), extra))
+    alone1 = [agis.estimate(g, p, o) for p, o in qs]
+    alone2 = [agis.estimate(g2, p, o) for p, o in qs]
+    s1 = agis.Server(g, 4 << 30, 4)
+    s2 = agis.Server(g2, 4 << 30, 4)
+    try:
+        t1, t2 = [], []
+        for p, o in qs:
+            t1.append(s1.submit(p, o))
+            t2.append(s2.submit(p, o))
+        r1 = wait_all(s1, t1)
+        r2 = wait_all(s2, t2)
+    finally:
+        s1.close()
+        s2.close()
+    for a, b in zip(alone1, r1):
+        for k in KEYS:
+            assert a[k] == b[k], k
+    for a, b in zip(alone2, r2):
+        for k in KEYS:
+            assert a[k] == b[k], k
+    g2.close()
