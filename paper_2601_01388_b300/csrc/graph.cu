@@ -461,21 +461,38 @@ int build_partial_rowp_layout(agis_graph *g)
     cudaStream_t st = g->ctx->stream;
     std::vector<int64_t> off((size_t)g->nv + 1);
     AGIS_CUDA_TRY(cudaMemcpy(off.data(), g->off, sizeof(int64_t) * off.size(), cudaMemcpyDeviceToHost));
-    std::vector<int32_t> order((size_t)g->nv);
-    for (int64_t v = 0; v < g->nv; ++v) order[(size_t)v] = (int32_t)v;
-    auto deg = [&](int32_t v) { return off[(size_t)v + 1] - off[(size_t)v]; };
-    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return deg(a) > deg(b); });
+    // Rows in descending degree, ascending id among equal degrees, are given a
+    // prefix while the budget lasts (stopping at the first row that does not fit).
+    // A degree histogram replaces the sort: whole degree classes are taken from
+    // the top, then the lowest ids of the class that no longer fits entirely.
+    auto deg = [&](int64_t v) { return off[(size_t)v + 1] - off[(size_t)v]; };
+    const int64_t max_d = g->max_deg;
+    std::vector<int64_t> hist((size_t)max_d + 1, 0);
+    for (int64_t v = 0; v < g->nv; ++v) hist[(size_t)deg(v)]++;
     const int64_t cap_entries = (int64_t)(g->rowp_budget / sizeof(uint64_t));
+    std::vector<int64_t> take((size_t)max_d + 1, 0), start((size_t)max_d + 1, 0), first_row((size_t)max_d + 1, 0);
+    int64_t used = 0, nrows = 0, min_deg = 0;
+    for (int64_t d = max_d; d >= 1; --d) {
+        if (hist[(size_t)d] == 0) continue;
+        const int64_t fit = (cap_entries - used) / d;
+        const int64_t t = std::min(hist[(size_t)d], std::max<int64_t>(fit, 0));
+        take[(size_t)d] = t;
+        start[(size_t)d] = used;
+        first_row[(size_t)d] = nrows;
+        if (t > 0) min_deg = d;
+        used += t * d;
+        nrows += t;
+        if (t < hist[(size_t)d]) break;
+    }
     std::vector<int64_t> base((size_t)g->nv, -1);
-    std::vector<int32_t> rows;
-    int64_t used = 0, min_deg = 0;
-    for (int32_t v : order) {
+    std::vector<int32_t> rows((size_t)nrows);
+    std::vector<int64_t> seen((size_t)max_d + 1, 0);
+    for (int64_t v = 0; v < g->nv; ++v) {
         const int64_t d = deg(v);
-        if (d == 0 || used + d > cap_entries) break;
-        base[(size_t)v] = used;
-        rows.push_back(v);
-        used += d;
-        min_deg = d;
+        if (d == 0 || seen[(size_t)d] >= take[(size_t)d]) continue;
+        const int64_t r = seen[(size_t)d]++;
+        base[(size_t)v] = start[(size_t)d] + r * d;
+        rows[(size_t)(first_row[(size_t)d] + r)] = (int32_t)v;
     }
     AGIS_CUDA_TRY(cudaMalloc(&g->rp_base, sizeof(int64_t) * (size_t)g->nv));
     AGIS_CUDA_TRY(cudaMemcpyAsync(g->rp_base, base.data(), sizeof(int64_t) * (size_t)g->nv, cudaMemcpyHostToDevice, st));
