@@ -634,6 +634,20 @@ static uint64_t anchor_sectors(const orc_query *Q, int i, const int32_t *tau, in
     return s;
 }
 
+/* Whether the cost model counts weight reads for step i.  A later step whose
+ * configuration has |F1| = |I_eff| = |F2| = 0 gives every candidate of S_tau the
+ * same quantised weight: each candidate is adjacent to the |B| backward vertices,
+ * so binom(d - |B|, 0) = 1 for all of them (|B| is 0 on an orientation).  A draw
+ * over equal weights is a draw of a position and needs no weight reads.  The
+ * arithmetic below still weighs such steps with q; only the sector count differs. */
+static int weights_read(const orc_query *Q, int i)
+{
+    const orc_plan *p = &Q->plan;
+    if (!Q->use_approx[i]) return 0;
+    if (i == 0) return 1;
+    return p->f1[i] != 0 || p->ieff[i] != 0 || p->f2[i] != 0;
+}
+
 /* Algorithmic-sector model of one step (a count of 32-byte sectors the step must
  * touch with no reuse; see the design notes):
  *   step 1: search over the (nv+1)-entry running-weight array (+1 for q(v_1));
@@ -642,7 +656,8 @@ static uint64_t anchor_sectors(const orc_query *Q, int i, const int32_t *tau, in
  *           the row under f_approx (+1 for q(v)), one sector for the chosen entry;
  *           several: a scan of the shortest backward row; for each other backward
  *           row the cheaper of reading it once (a merge) and one membership search
- *           per scanned entry; one q gather per candidate under f_approx. */
+ *           per scanned entry; one q gather per candidate under f_approx
+ *           (weights_read: none where the weights are equal on S_tau). */
 static uint64_t step_sectors(const orc_query *Q, int i, const int32_t *tau, int64_t nS)
 {
     const orc_plan *p = &Q->plan;
@@ -652,7 +667,7 @@ static uint64_t step_sectors(const orc_query *Q, int i, const int32_t *tau, int6
     if (nb == 1) {
         int64_t d = Q->off[tau[p->back[i][0]] + 1] - Q->off[tau[p->back[i][0]]];
         s += (uint64_t)(i - 1) * sec_search(d, 4);
-        if (Q->use_approx[i]) s += sec_search(d, 8) + 1;
+        if (weights_read(Q, i)) s += sec_search(d, 8) + 1;
         s += 1;
         return s;
     }
@@ -672,7 +687,7 @@ static uint64_t step_sectors(const orc_query *Q, int i, const int32_t *tau, int6
         uint64_t search_each = (uint64_t)da * sec_search(m, 4);
         s += read_once < search_each ? read_once : search_each;
     }
-    if (Q->use_approx[i]) s += (uint64_t)nS;
+    if (weights_read(Q, i)) s += (uint64_t)nS;
     return s;
 }
 

@@ -45,6 +45,7 @@ struct DevStep {
 };
 
 constexpr int32_t kFlagAnchor = 1;   // DevQuery::flags: anchor draw on several-backward steps
+constexpr int32_t kFlagPlainLists = 2;  // DevQuery::flags: no candidate-list step weighs its survivors
 
 struct DevQuery {
     int32_t k;
@@ -214,6 +215,12 @@ int make_dev_query(agis_graph *g, const agis_pattern *p, const agis_opts *o, Dev
 // weight configuration of step i: the factors that `terms` drops get exponent 0, and
 // on an oriented graph |B| is 0 (no backward vertex lies in a later vertex's out-row)
 void effective_cfg(const agis_pattern *p, int i, int32_t terms, bool oriented, int32_t out[4]);
+// true when step i's f_approx weight is the same for every candidate of its S_tau
+// build, so the step draws by position with no table (see runtime.cu)
+bool step_weights_flat(const agis_pattern *p, int i, const agis_opts *o, bool oriented);
+// true when step i reads an f_approx weight table: D(i) chose f_approx and the
+// weights are not flat
+bool step_uses_table(const agis_pattern *p, int i, const agis_opts *o, bool oriented, const uint8_t *use);
 int ensure_buffers(LaunchBuffers &lb, size_t n_queries, size_t n_items);
 int grid_for(agis_graph *g, size_t n_items);
 int ensure_scratch(agis_graph *g, LaunchBuffers &lb, int grid);

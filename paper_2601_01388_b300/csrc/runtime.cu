@@ -167,6 +167,29 @@ void effective_cfg(const agis_pattern *p, int i, int32_t terms, bool oriented, i
     out[3] = (terms == 0 || (terms & 4)) ? p->cfg[i][3] : 0;
 }
 
+// With |F1| = |I_eff| = |F2| = 0 in the effective configuration, Eq.
+// probability_function is binom(d - |B|, 0) = 1 for d >= |B| and an intended zero
+// below.  Every candidate of a later step's S_tau is adjacent to the |B| distinct
+// backward vertices, so d >= |B| (on an orientation |B| is 0): the quantised weight
+// is one constant c on all of S_tau.  The draw r = floor(U * |S| c / 2^128) then
+// picks position floor(r / c) = floor(U * |S| / 2^128), the position draw, and
+// W / q = |S| exactly, so such a step runs as f_uniform with identical results and
+// no weight reads.  Step 1 is excluded (f_uniform is edge-uniform there), and so is
+// an anchor draw, whose proposal row may hold vertices of degree below |B|.
+bool step_weights_flat(const agis_pattern *p, int i, const agis_opts *o, bool oriented)
+{
+    if (i == 0) return false;
+    if (o->anchor && p->nback[i] >= 2) return false;
+    int32_t cfg[4];
+    effective_cfg(p, i, o->terms, oriented, cfg);
+    return cfg[1] == 0 && cfg[2] == 0 && cfg[3] == 0;
+}
+
+bool step_uses_table(const agis_pattern *p, int i, const agis_opts *o, bool oriented, const uint8_t *use)
+{
+    return use[i] && !step_weights_flat(p, i, o, oriented);
+}
+
 int make_dev_query(agis_graph *g, const agis_pattern *p, const agis_opts *o, DevQuery *dq,
                    double *t_prep)
 {
@@ -186,7 +209,7 @@ int make_dev_query(agis_graph *g, const agis_pattern *p, const agis_opts *o, Dev
     for (int i = 0; i < p->k; ++i) {
         DevStep &s = dq->step[i];
         s.nb = p->nback[i];
-        s.approx = use[i];
+        s.approx = step_uses_table(p, i, o, g->oriented, use);
         for (int j = 0; j < p->nback[i] && j < kMaxK; ++j) s.back[j] = (int8_t)p->back[i][j];
         if (i >= 2) {
             // back(i) == back(i-1) + {i-1}?
@@ -195,7 +218,7 @@ int make_dev_query(agis_graph *g, const agis_pattern *p, const agis_opts *o, Dev
             for (int j = 0; j < p->nback[i - 1]; ++j) mp |= 1u << p->back[i - 1][j];
             s.inc = (int8_t)(mi == (mp | (1u << (i - 1))) ? 1 : 0);
         }
-        if (!use[i]) continue;
+        if (!s.approx) continue;
         const size_t before = g->tables.size();
         WeightTable *t = nullptr;
         // a row-prefix table makes single-backward draws a search; when the full table
@@ -217,6 +240,15 @@ int make_dev_query(agis_graph *g, const agis_pattern *p, const agis_opts *o, Dev
         }
     }
     if (!use[0]) dq->W1 = (uint64_t)g->nnz;
+    // a step draws from a candidate list when it has several backward vertices, or
+    // one without a row prefix for every row; if none of those lists is weighted,
+    // the sampler filters survivor ids only
+    bool weighted_lists = false;
+    for (int i = 1; i < p->k; ++i) {
+        const DevStep &s = dq->step[i];
+        if (s.approx && (s.nb >= 2 || s.rp_mode != 1)) weighted_lists = true;
+    }
+    if (!weighted_lists) dq->flags |= kFlagPlainLists;
     if (built) AGIS_CUDA_TRY(cudaStreamSynchronize(g->ctx->stream));
     if (t_prep) *t_prep += now_s() - t0;
     return AGIS_OK;

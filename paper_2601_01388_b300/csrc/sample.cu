@@ -681,6 +681,7 @@ __device__ TrialOut run_trial(const GraphView &g, const DevQuery &Q, uint64_t t,
             // S of the previous step is reusable when this step's backward set is the
             // previous one plus the previous vertex: S_i = S_{i-1} & N(v_{i-1})
             const bool reuse = S.inc && cur >= 0 && !anch;
+            const bool weigh = S.approx || !(Q.flags & kFlagPlainLists);
             const uint32_t n_src = reuse ? n_cur : (uint32_t)da;
             bool listed = false;
             int nxt = reuse ? 1 - cur : 0;
@@ -704,19 +705,29 @@ __device__ TrialOut run_trial(const GraphView &g, const DevQuery &Q, uint64_t t,
                         m = o_len[pss];
                         Rb = o_bits[pss];
                     }
-                    if (pss == passes - 1) {
+                    // The last pass forms the running weights of an f_approx list.  A
+                    // position draw needs survivor ids alone, but only a query none of
+                    // whose lists is weighted filters ids only: running both filter
+                    // instances in one query cost more instruction fetch in this large
+                    // kernel than the running weights save (cliques ran 2-5% slower),
+                    // so such a query keeps counts in the weighted instance.
+                    const bool last = pss == passes - 1;
+                    if (last && weigh) {
                         n = filter_list<true>(src, n, R, m, Rb, tau_s, pss == 0 ? tau_n : 0, ws.xs[nxt],
                                               ws.pw[nxt], ws.cap, S.q, S.approx != 0, &Wl, lane);
                     } else {
                         n = filter_list<false>(src, n, R, m, Rb, tau_s, pss == 0 ? tau_n : 0, ws.xs[nxt],
                                                ws.pw[nxt], ws.cap, S.q, S.approx != 0, nullptr, lane);
-                        src = ws.xs[nxt];
-                        nxt = 1 - nxt;
+                        if (!last) {
+                            src = ws.xs[nxt];
+                            nxt = 1 - nxt;
+                        }
                     }
                     if (n > ws.cap) break;
                 }
                 __syncwarp();
                 listed = n <= ws.cap;
+                if (listed && !weigh) Wl = n;
             }
             if (listed) {
                 if (S.approx && S.nb > 1 && !anch) sec += n;
@@ -725,9 +736,10 @@ __device__ TrialOut run_trial(const GraphView &g, const DevQuery &Q, uint64_t t,
                 n_cur = n;
                 if (W == 0) { out.sectors = sec; return out; }
                 const uint64_t r = draw_below(W, t, (uint64_t)(i + 1), kStreamTrial, Q.seed);
-                const int64_t j = warp_find(ws.pw[cur], n, r, 0u, 0, 0, nullptr, lane);
+                // equal weights: the r-th survivor (r < W = n)
+                const int64_t j = S.approx ? warp_find(ws.pw[cur], n, r, 0u, 0, 0, nullptr, lane) : (int64_t)r;
                 v = ws.xs[cur][j];
-                qv = ws.pw[cur][j] - (j > 0 ? ws.pw[cur][j - 1] : 0);
+                qv = S.approx ? ws.pw[cur][j] - (j > 0 ? ws.pw[cur][j - 1] : 0) : 1u;
                 if (anch) {
                     cur = -1;
                     if (!closes_all(g, S, tau_s, jb, v, lane)) { out.sectors = sec; return out; }

@@ -48,7 +48,7 @@ namespace {
 
 constexpr size_t kMaxWaiting = 65536;
 
-// Device bytes a query would add: the parts of its f_approx steps' tables that are
+// Device bytes a query would add: the parts of the tables its f_approx steps read that are
 // not resident yet (q per vertex; a vertex prefix for step 1; a row prefix for
 // single-backward steps while the graph's row-prefix budget allows one).
 size_t extra_bytes(agis_graph *g, const agis_pattern &p, const agis_opts &o)
@@ -60,7 +60,7 @@ size_t extra_bytes(agis_graph *g, const agis_pattern &p, const agis_opts &o)
     const size_t rowp_bytes = rowp_full_fits(g) ? sizeof(uint64_t) * (size_t)g->nnz
                                                  : std::min<size_t>(g->rowp_budget, sizeof(uint64_t) * (size_t)g->nnz);
     for (int i = 0; i < p.k; ++i) {
-        if (!use[i]) continue;
+        if (!step_uses_table(&p, i, &o, g->oriented, use)) continue;
         int32_t cfg[4];
         effective_cfg(&p, i, o.terms, g->oriented, cfg);
         auto &f = need[cfg_key(cfg)];
@@ -148,7 +148,7 @@ void scheduler(agis_server *s)
                 uint8_t use[kMaxK];
                 agis_pattern_decide(&q->pat, q->opts.mode, q->opts.beta, use);
                 for (int i = 0; i < q->pat.k; ++i) {
-                    if (!use[i]) continue;
+                    if (!step_uses_table(&q->pat, i, &q->opts, g->oriented, use)) continue;
                     int32_t cfg[4];
                     effective_cfg(&q->pat, i, q->opts.terms, g->oriented, cfg);
                     const uint64_t key = cfg_key(cfg);

@@ -88,13 +88,15 @@ def test_admission_by_memory(agis, setup):
     alone = [agis.estimate(g, p, o) for p, o in qs]
     g.drop_tables()
     # room for the largest single query's tables (q per vertex, a vertex prefix for
-    # step 1, a row prefix per single-backward f_approx step), not for all of them
+    # step 1, a row prefix per single-backward f_approx step), not for all of them;
+    # a later step whose configuration has no F1, I1 or F2 term weighs its candidates
+    # equally and reads no table
     def need(p, o):
         info = p.info()
         use = p.decide(o.mode, o.beta)
         cfgs = {}
         for i in range(info["k"]):
-            if use[i]:
+            if use[i] and (i == 0 or any(info["cfg"][i][1:])):
                 c = cfgs.setdefault(info["cfg"][i], [False, False])
                 c[0] |= i == 0
                 c[1] |= i > 0 and len(info["back"][i]) == 1

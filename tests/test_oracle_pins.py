@@ -90,6 +90,35 @@ def test_draw_below_uniform_chi2(oracle_mod):
     assert scipy.stats.chisquare(counts).pvalue > 1e-4
 
 
+def test_draw_over_equal_weights_is_a_position_draw(oracle_mod):
+    # n candidates of equal weight c: the weighted draw picks position floor(r / c)
+    # with r = floor(U n c / 2^128), which is floor(U n / 2^128), the draw over n
+    # (nested floors); and W / q = n c / c is exactly n in double.  A step whose
+    # weights are equal on every candidate can therefore draw by position.
+    rng = np.random.default_rng(3)
+    for n in [1, 2, 3, 7, 1000, 65537, 2 ** 31 - 1]:
+        for c in [1, 2, 3, 2 ** 20, 2 ** 30 + 5, (2 ** 62 - 1) // n]:
+            if c < 1 or n * c >= 2 ** 62:
+                continue
+            for t in rng.integers(0, 2 ** 40, size=6):
+                t = int(t)
+                assert oracle_mod.draw_below(n * c, t, 4, 1, 9) // c == oracle_mod.draw_below(n, t, 4, 1, 9)
+            assert float(n * c) / float(c) == float(n)
+
+
+@pytest.mark.parametrize("cfg", [(1, 0, 0, 0), (2, 0, 0, 0), (3, 0, 0, 0), (4, 0, 0, 0)])
+def test_configs_without_exponents_weigh_candidates_equally(oracle_mod, cfg):
+    # binom(d - |B|, 0) = 1 from d = |B| on, 0 below: one constant on every vertex
+    # of degree >= |B|, which every candidate of a step with |B| backward edges has
+    off, cols = I.rmat_graph(9, 8, seed=5)
+    nsum, hits = oracle_mod.graph_stats(off, cols, 1)
+    q, shift = oracle_mod.weight_table(off, nsum, hits, 2.0 ** -10, cfg)
+    deg = np.diff(off)
+    assert (q[deg < cfg[0]] == 0).all()
+    vals = np.unique(q[deg >= cfg[0]])
+    assert len(vals) == 1 and vals[0] > 0
+
+
 @pytest.mark.parametrize("d", [2, 3, 4, 7])
 def test_cc_pair_is_bijection_on_ordered_distinct_pairs(oracle_mod, d):
     pairs = [oracle_mod.cc_pair(d, r) for r in range(d * (d - 1))]
