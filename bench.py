@@ -171,6 +171,13 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ inputs
 
+def workload_name(args, names):
+    """The workload both arms report (the reference arm times a bounded sample of it)."""
+    return (f"plain per-query launches: R-MAT scale {args.scale} (edge factor 16, a=0.57 b=0.19 c=0.19), "
+            f"patterns {', '.join(names)}, 2^{args.log2_trials} trials each, D^pi (beta 0.8), "
+            f"FP64 estimate and variance")
+
+
 def make_workload(scale):
     from paper_2601_01388_b300 import inputs as I
     t = time.time()
@@ -850,9 +857,7 @@ def run_gpu(args, world, rank, local):
         "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"plain per-query launches: R-MAT scale {args.scale} (edge factor 16, "
-                               f"a=0.57 b=0.19 c=0.19), patterns {', '.join(names)}, 2^{args.log2_trials} "
-                               f"trials each, D^pi (beta 0.8), FP64 estimate and variance",
+        "config": {"workload": workload_name(args, names),
                    "nv": info["nv"], "nnz": info["nnz"], "max_degree": info["max_degree"],
                    "trials_per_pattern": trials, "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (CSR %.2f GB plus weight tables)" % ((off.nbytes + cols.nbytes) / 1e9),
@@ -912,9 +917,8 @@ def run_reference(args, world, rank):
     return {"metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": f"plain per-query launches: R-MAT scale {args.scale}, patterns "
-                                   f"{', '.join(names)}, bounded sample of 2^{args.log2_trials} trials each",
-                       "parallelism": "host processes"},
+            "config": {"workload": workload_name(args, names), "trials_per_pattern": 1 << args.log2_trials,
+                       "parallelism": "host processes", "sampled": f"{per} trials of each pattern per step"},
             "cpu_baseline": cpu,
             "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
