@@ -344,6 +344,25 @@ def test_counts_divided_by_aut_are_integers(oracle_mod, gname):
         assert c % oracle_mod.compile_pattern(k, edges)["aut"] == 0
 
 
+@pytest.mark.parametrize("name", ["triangle", "4-cycle", "house"])
+def test_gnp_mean_count_matches_expectation(oracle_mod, name):
+    # over G(n, p) instances every injective map is an embedding with probability
+    # p^|E_P|, so E[C(G,P)] = n^(k) p^|E_P|: the brute-force counts and the oracle's
+    # estimates (unbiased per instance, Thm. 2) must both average to it
+    n, p, reps = 10, 0.5, 240
+    k, edges = I.PATTERNS[name]
+    expect = falling(n, k) * p ** len(edges)
+    exact, est = [], []
+    for seed in range(reps):
+        off, cols = I.gnp_graph(n, p, 1000 + seed)
+        exact.append(oracle_mod.bruteforce_count(off, cols, k, edges))
+        q = oracle_mod.Query(off, cols, k, edges, mode=oracle_mod.MODE_APPROX, seed=seed + 1)
+        est.append(q.sums(0, 512)["sum_x"] / 512)
+    for vals in (np.array(exact, dtype=float), np.array(est)):
+        se = vals.std(ddof=1) / np.sqrt(reps)
+        assert abs(vals.mean() - expect) <= 4.5 * se, (vals.mean(), expect, se)
+
+
 # ---------------------------------------------------------------- sampler (Alg. 3, Thm. 2)
 
 @pytest.mark.parametrize("gname", sorted(TINY_GRAPHS))
