@@ -256,6 +256,14 @@ def _orc_sample(name, seed, first, count):
     return count, time.time() - t, s["sum_x"]
 
 
+def host_cores():
+    """Cores this process may run on (its CPU affinity), which may be fewer than the host has."""
+    try:
+        return max(1, len(os.sched_getaffinity(0)))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
 class OraclePool:
     """The CPU oracle on all host cores: one spawn-started process per core, the CSR
     in shared memory, preprocessing split by vertex ranges and sampling split by
@@ -265,7 +273,7 @@ class OraclePool:
         import multiprocessing as mp
         from multiprocessing import shared_memory
         self.nv, self.nnz = len(off) - 1, len(cols)
-        self.procs = procs or os.cpu_count() or 1
+        self.procs = procs or host_cores()
         self.shm = []
         arrs = []
         for a in (off, cols):
