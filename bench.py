@@ -179,6 +179,15 @@ def workload_name(args, names):
             f"FP64 estimate and variance")
 
 
+L2_BYTES = 126 * 1000 * 1000     # B300 L2
+
+
+def l2_note(csr_bytes):
+    """How the timed inputs compare with L2 (nothing is flushed between steps)."""
+    rel = "larger" if csr_bytes > L2_BYTES else "not larger"
+    return f"inputs {rel} than L2 (CSR {csr_bytes / 1e9:.2f} GB plus weight tables; L2 126 MB, not flushed)"
+
+
 def make_workload(scale):
     from paper_2601_01388_b300 import inputs as I
     t = time.time()
@@ -869,7 +878,7 @@ def run_gpu(args, world, rank, local):
         "config": {"workload": workload_name(args, names),
                    "nv": info["nv"], "nnz": info["nnz"], "max_degree": info["max_degree"],
                    "trials_per_pattern": trials, "parallelism": f"replicas x{world}",
-                   "l2": "inputs larger than L2 (CSR %.2f GB plus weight tables)" % ((off.nbytes + cols.nbytes) / 1e9),
+                   "l2": l2_note(off.nbytes + cols.nbytes),
                    "graph_generation_s": t_gen},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "kernel": "sample_kernel",
