@@ -363,6 +363,59 @@ def test_gnp_mean_count_matches_expectation(oracle_mod, name):
         assert abs(vals.mean() - expect) <= 4.5 * se, (vals.mean(), expect, se)
 
 
+def _sec_search(L, w):
+    nbytes = max(L, 1) * w
+    if nbytes <= 32:
+        return 1
+    return math.ceil(math.log2(-(-nbytes // 32))) + 1
+
+
+@pytest.mark.parametrize("name", ["triangle", "4-cycle", "house", "4-clique", "3-path", "5-cycle",
+                                  "diamond", "chordal-5-cycle"])
+@pytest.mark.parametrize("mode", MODES)
+def test_sector_model_restated(oracle_mod, name, mode):
+    # The algorithmic-sector model (this build's cost model; the kernel counts the
+    # same one, checked on the GPU) restated from its definition, trial by trial
+    # from the oracle's trajectories: step 1 a search over the nv+1 running weights
+    # (+1 for q); one backward edge: offsets, i-1 membership searches in the row, a
+    # row-prefix search and q where weights are read, the chosen entry; several: one
+    # offsets sector each, a scan of the shortest row, per other row the cheaper of a
+    # merge and one search per scanned entry, one q per candidate where weights are
+    # read.  Weights are read under f_approx except on a later step whose
+    # configuration has no F1, I1 or F2 term (equal weights on S_tau).
+    off, cols = I.rmat_graph(8, 8, seed=9)
+    k, edges = I.PATTERNS[name]
+    q = oracle_mod.Query(off, cols, k, edges, mode=mode, seed=5)
+    info = q.info()
+    back = oracle_mod.compile_pattern(k, edges)["back"]
+    nv = len(off) - 1
+    deg = np.diff(off)
+    adj = [set(cols[off[v]:off[v + 1]].tolist()) for v in range(nv)]
+    emb, hit, x, sec = q.trials(0, 400)
+    for t in range(len(emb)):
+        tau = emb[t]
+        want = _sec_search(nv + 1, 8) + (1 if info["use_approx"][0] else 0)
+        for i in range(1, k):
+            reads = info["use_approx"][i] and any(info["cfg"][i][1:])
+            rows = [int(tau[j]) for j in back[i]]
+            if len(rows) == 1:
+                d = int(deg[rows[0]])
+                want += 1 + (i - 1) * _sec_search(d, 4) + ((_sec_search(d, 8) + 1) if reads else 0) + 1
+            else:
+                ds = [int(deg[u]) for u in rows]
+                a = ds.index(min(ds))
+                want += len(rows) + -(-4 * ds[a] // 32)
+                for b, m in enumerate(ds):
+                    if b != a:
+                        want += min(-(-4 * max(m, 1) // 32), ds[a] * _sec_search(m, 4))
+                if reads:
+                    S = set.intersection(*[adj[u] for u in rows]) - set(int(v) for v in tau[:i])
+                    want += len(S)
+            if tau[i] < 0:
+                break
+        assert sec[t] == want, (t, list(tau))
+
+
 # ---------------------------------------------------------------- sampler (Alg. 3, Thm. 2)
 
 @pytest.mark.parametrize("gname", sorted(TINY_GRAPHS))
