@@ -4,17 +4,26 @@
 Workload (plain per-query launches): R-MAT scale 22 (4.2M vertices, edge factor
 16, a=0.57 b=0.19 c=0.19, symmetrised, deduplicated, int32 columns), patterns
 4-clique, 5-cycle, house and 5-clique, 2^28 trials each under the decision
-function D^pi (beta = 0.8), FP64 estimate and variance.  One step is one pass
-of the whole path over that input: Sec. 4.4 preprocessing (neighbour-degree sums
-and sampled clustering coefficients), the f_approx weight tables and prefix
-sums, 2^28 Alg. 3 trials per pattern with per-tile FP64 reductions, and the
-final sums.  Inputs are synthetic; the paper's data sets are not available.
+function D^pi (beta = 0.8), FP64 estimate and variance.  One step is one plain
+per-query launch of the whole path for one pattern, the patterns taken in turn
+(step j runs pattern j mod 4, so every four steps cover the workload once):
+Sec. 4.4 preprocessing (neighbour-degree sums, sampled clustering coefficients,
+hub bitmaps), the pattern's f_approx weight tables and prefix sums, its 2^28
+Alg. 3 trials with per-tile FP64 reductions, and the tile sums read back to the
+host.  Warm-up steps run the same path at a smaller trial budget (they only
+have to build the kernel instances, scratch and tables once).  Inputs are
+synthetic; the paper's data sets are not available.
 
-Also reported: the same metric end to end through the C ABI from host buffers
-(`e2e`), time to +-1% error at 95% confidence (Alg. 1, eps = 0.01, delta = 0.05)
-for plain, batched and served forms, the sampler kernel's achieved bandwidth
-against the measured HBM copy peak (`roofline`), and the CPU oracle on a bounded
-sample of the same workload on this host's cores (`cpu_baseline`).
+Also reported: the same metric end to end through the C ABI from pinned host
+buffers (`e2e`: graph upload, preprocessing, tables, the estimate call and its
+result, one rotation over the patterns), time to +-1% error at 95% confidence
+(Alg. 1, eps = 0.01, delta = 0.05) for plain, batched and served forms, the
+batching configuration (64 queries on a scale-24 R-MAT, each to +-1% or its
+budget, one persistent batched call against 64 plain calls), the sampler
+kernel's algorithmic bandwidth against the measured HBM copy peak (`roofline`),
+and the CPU oracle on a bounded sample of the same workload on this host's
+cores (`cpu_baseline`).  Every leg after the timed loop is skipped, and says
+so, if the run would pass its deadline.
 
 --impl reference times the CPU oracle instead (the reference arm of this
 repository; the paper's own code is not available here).
@@ -22,6 +31,7 @@ repository; the paper's own code is not available here).
 from __future__ import annotations
 
 import argparse
+import ctypes
 import hashlib
 import json
 import math
@@ -42,24 +52,41 @@ PATTERN_NAMES = ["4-clique", "5-cycle", "house", "5-clique"]
 CMIN = 2.0 ** -10
 
 
-def parse_args():
+def parse_args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4,
+                    help="timed steps; step j is the full query of pattern j mod (number of patterns)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="agis", choices=["agis", "reference"])
     ap.add_argument("--scale", type=int, default=22)
     ap.add_argument("--log2-trials", type=int, default=28)
+    ap.add_argument("--warmup-log2-trials", type=int, default=22,
+                    help="trials of a warm-up step (same path, smaller budget)")
     ap.add_argument("--patterns", default=",".join(PATTERN_NAMES))
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=0,
+                    help="end-to-end steps (default: one per pattern)")
     ap.add_argument("--no-tte", action="store_true")
+    ap.add_argument("--tte-chunk-log2", type=int, default=12,
+                    help="Alg. 1 checkpoint spacing (and first checkpoint) of the time-to-+-1%% legs")
+    ap.add_argument("--tte-cap-log2", type=int, default=24, help="trial cap of an f_approx time-to-+-1%% query")
+    ap.add_argument("--uniform-cap-log2", type=int, default=24,
+                    help="trial cap of an f_uniform time-to-+-1%% query (the trials it would need are extrapolated)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--deadline-s", type=float, default=1500.0,
+                    help="legs after the timed loop are skipped when their planned time would pass this")
     ap.add_argument("--json-out", default="")
-    ap.add_argument("--batch64", action="store_true",
-                    help="also run the batching configuration: R-MAT scale 24 built on the device, 64 "
-                         "queries with budgets 2^16..2^26, one autotuned persistent launch vs 64 plain launches")
+    ap.add_argument("--summarize-ncu", default="",
+                    help="(no GPU) turn an ncu CSV of sampler launches into the committed JSON traffic summary")
+    ap.add_argument("--summary-out", default="")
+    ap.add_argument("--ncu-command", default="", help="the ncu command line recorded in the summary")
+    ap.add_argument("--no-batch64", dest="batch64", action="store_false",
+                    help="skip the batching configuration: R-MAT scale 24 built on the device, 64 queries to "
+                         "+-1%% with budgets 2^16..2^26 as caps, one batched call vs 64 plain calls")
     ap.add_argument("--batch-scale", type=int, default=24)
+    ap.add_argument("--batch-eps", type=float, default=0.01)
     ap.add_argument("--large", action="store_true",
                     help="also run the large-graph configuration: R-MAT scale 28, edge factor 32, built on the "
                          "device; 6-clique and 7-cycle to +-1%% under f_approx and f_uniform (2^30-trial budget)")
@@ -80,7 +107,7 @@ def parse_args():
     ap.add_argument("--ablation", action="store_true",
                     help="also run the f_approx term ablation and the beta sweep on the bench graph "
                          "(time and trials to +-1%%)")
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 # ------------------------------------------------------------------ distributed (replicas only)
@@ -211,19 +238,99 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def profile_traffic(trials_per_launch):
-    """DRAM bytes per trial of the sampler from the committed ncu summary, if it was
-    taken on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", "sample_kernel_rmat_s22.md")
+TRAFFIC_SUMMARY = os.path.join(ROOT, "profiles", "sample_kernel_dram_rmat_s22.json")
+
+
+def profile_traffic(path=TRAFFIC_SUMMARY):
+    """Per-pattern DRAM bytes per trial of the sampler from the committed ncu summary
+    (written by --summarize-ncu), if it was taken on the current kernel sources and
+    the same workload; else None."""
     if not os.path.exists(path):
         return None
-    text = open(path).read()
-    if f"kernel sources sha256[:16]: {kernel_source_hash()}" not in text:
+    d = json.load(open(path))
+    if d.get("kernel_sources_sha16") != kernel_source_hash():
         return None
-    for line in text.splitlines():
-        if line.strip().startswith("dram_bytes_per_trial:"):
-            return float(line.split(":")[1].split()[0]) * trials_per_launch
-    return None
+    return {n: v["dram_bytes_per_trial"] for n, v in d.get("per_pattern", {}).items()}
+
+
+def summarize_ncu(csv_path, out_path, names, trials, command, workload):
+    """Reads an ncu --csv log of sampler launches (metrics dram__bytes_read.sum,
+    dram__bytes_write.sum, gpu__time_duration.sum), one launch per pattern in the
+    benchmark's order, and writes the per-pattern JSON summary the benchmark reads."""
+    import csv
+    rows = []
+    with open(csv_path) as f:
+        lines = [ln for ln in f if ln.startswith('"')]
+    for r in csv.DictReader(lines):
+        rows.append(r)
+    launches = {}
+    for r in rows:
+        if "sample_kernel" not in r.get("Kernel Name", ""):
+            continue
+        lid = int(r["ID"])
+        m = launches.setdefault(lid, {"kernel": r["Kernel Name"]})
+        val = float(r["Metric Value"].replace(",", ""))
+        unit = r.get("Metric Unit", "")
+        scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "Tbyte": 1e12,
+                 "nsecond": 1, "usecond": 1e3, "msecond": 1e6, "second": 1e9}.get(unit, 1)
+        m[r["Metric Name"]] = val * scale
+    ids = sorted(launches)
+    per = {}
+    for j, lid in enumerate(ids):
+        name = names[j % len(names)]
+        m = launches[lid]
+        rd, wr = m.get("dram__bytes_read.sum", 0.0), m.get("dram__bytes_write.sum", 0.0)
+        e = per.setdefault(name, {"launches": 0, "trials": 0, "dram_read_bytes": 0.0, "dram_write_bytes": 0.0,
+                                  "duration_ns": 0.0})
+        e["launches"] += 1
+        e["trials"] += trials
+        e["dram_read_bytes"] += rd
+        e["dram_write_bytes"] += wr
+        e["duration_ns"] += m.get("gpu__time_duration.sum", 0.0)
+    for e in per.values():
+        e["dram_bytes_per_trial"] = (e["dram_read_bytes"] + e["dram_write_bytes"]) / e["trials"]
+        e["dram_gbs"] = (e["dram_read_bytes"] + e["dram_write_bytes"]) / e["duration_ns"] if e["duration_ns"] else None
+    out = {"kernel": "sample_kernel", "kernel_sources_sha16": kernel_source_hash(), "workload": workload,
+           "trials_per_launch": trials, "command": command, "per_pattern": per,
+           "note": "ncu serialises launches: durations are for comparison only"}
+    with open(out_path, "w") as f:
+        json.dump(out, f, indent=1)
+        f.write("\n")
+    return out
+
+
+# ------------------------------------------------------------------ wall-time plan
+
+# Rates the plan below assumes (samples/s): floors under the measured rates of the
+# committed sampler, on the benchmark graph and on the scale-24 batching graph.
+RATE_FLOOR = {"bench": 8.0e6, "batch": 4.0e6}
+FIXED_S = 150.0      # torch import, library build check, host graph generation, upload, oracle pool, probe
+
+
+def batch_budget_trials(n=64, seed=1):
+    from paper_2601_01388_b300 import inputs as I
+    return sum(b for _, _, b in I.batch_queries(n, seed=seed))
+
+
+def plan_seconds(args, rates=RATE_FLOOR):
+    """Upper bounds, per leg, of the wall time of a default run with these arguments:
+    every capped query is assumed to run to its cap at the floor rates."""
+    names = [n for n in args.patterns.split(",") if n]
+    full = float(1 << args.log2_trials)
+    p = {"fixed": FIXED_S,
+         "warmup": args.warmup * float(1 << args.warmup_log2_trials) / rates["bench"],
+         "timed": args.steps * full / rates["bench"]}
+    if not args.no_e2e:
+        p["e2e"] = (args.e2e_steps or len(names)) * full / rates["bench"]
+    if not args.no_tte:
+        # plain, batched and served forms under f_approx, then f_uniform alone
+        p["tte"] = (3 * len(names) * float(1 << args.tte_cap_log2) +
+                    len(names) * float(1 << args.uniform_cap_log2)) / rates["bench"]
+    if args.batch64:
+        p["batch64"] = 20.0 + 2 * batch_budget_trials() / rates["batch"]
+    if not args.no_cpu:
+        p["cpu"] = 4 * args.cpu_seconds + 10.0
+    return p
 
 
 # ------------------------------------------------------------------ CPU oracle
@@ -423,12 +530,15 @@ def serving_configs(agis, ctx, seconds):
 
 # ------------------------------------------------------------------ batching configuration
 
-def batch64(agis, ctx, scale, stream):
-    """64 pattern queries (cliques, cycles, paths, stars of 3-7 vertices, tailed
-    triangle, diamond, chordal 5-cycle) with fixed trial budgets log-uniform in
-    2^16..2^26 on an R-MAT graph generated on the device: all of them in one
-    persistent launch (after the autotuner picks CTAs per SM and tiles per item)
-    against 64 plain launches."""
+def batch64(agis, ctx, scale, eps=0.01, chunk_log2=12, deadline=None):
+    """The batching configuration: 64 pattern queries (cliques, cycles, paths,
+    stars of 3-7 vertices, tailed triangle, diamond, chordal 5-cycle) on an R-MAT
+    graph generated on the device, each run to +-eps at 95% confidence by Alg. 1
+    with its budget (log-uniform in 2^16..2^26) as a cap: 64 plain calls (one
+    query at a time) against one batched call (all queries share every epoch's
+    persistent launch, after the autotuner picks CTAs per SM and tiles per item),
+    then the same 64 queries submitted at once to a server.  Every query's result
+    must be identical in the three forms."""
     import torch
     from paper_2601_01388_b300 import inputs as I
     t0 = time.perf_counter()
@@ -439,28 +549,65 @@ def batch64(agis, ctx, scale, stream):
     t_prep = time.perf_counter() - t0
     qs = I.batch_queries(64, seed=1)
     pats = [agis.Pattern(*pat) for _, pat, _ in qs]
-    opts = [agis.default_opts(mode=0, seed=500 + i, eps=0.0, max_trials=b) for i, (_, _, b) in enumerate(qs)]
+    chunk = 1 << chunk_log2
+    opts = [agis.default_opts(mode=0, seed=500 + i, eps=eps, delta=0.05, chunk_trials=chunk, min_trials=chunk,
+                              max_trials=b) for i, (_, _, b) in enumerate(qs)]
     t0 = time.perf_counter()
     for p, o in zip(pats, opts):
         agis.prepare(g, p, o)
     t_tables = time.perf_counter() - t0
     best, span = agis.autotune(g, pats, opts, 1 << 15)
-    total = sum(b for _, _, b in qs)
     torch.cuda.synchronize()
+    out = {"generate_s": t_gen, "preprocess_s": t_prep, "tables_s": t_tables, "queries": len(qs),
+           "eps": eps, "delta": 0.05, "chunk_trials": chunk, "budget_trials": int(sum(b for _, _, b in qs)),
+           "autotuned_ctas_per_sm": best, "autotuned_tiles_per_item": span}
     t0 = time.perf_counter()
-    plain = [agis.estimate(g, p, o) for p, o in zip(pats, opts)]
-    t_plain = time.perf_counter() - t0
+    plain = []
+    for p, o in zip(pats, opts):
+        t1 = time.perf_counter()
+        r = agis.estimate(g, p, o)
+        r["s"] = time.perf_counter() - t1
+        plain.append(r)
+    out["plain_s"] = time.perf_counter() - t0
     t0 = time.perf_counter()
     batched = agis.estimate_batch(g, pats, opts)
-    t_batch = time.perf_counter() - t0
-    same = all(a["sum_x"] == b["sum_x"] and a["hits"] == b["hits"] for a, b in zip(plain, batched))
+    out["batched_s"] = time.perf_counter() - t0
+    served = None
+    if deadline is None or time.perf_counter() + out["batched_s"] * 1.5 < deadline:
+        srv = agis.Server(g, 200 << 30, 64)
+        t0 = time.perf_counter()
+        tickets = [srv.submit(p, o) for p, o in zip(pats, opts)]
+        done = {}
+        while len(done) < len(tickets):
+            for tk in tickets:
+                if tk not in done:
+                    r = srv.poll(tk)
+                    if r is not None:
+                        done[tk] = r
+            time.sleep(0.0005)
+        out["served_s"] = time.perf_counter() - t0
+        out["served_epochs"] = srv.stats()["epochs"]
+        srv.close()
+        served = [done[tk] for tk in tickets]
+    keys = ("trials", "hits", "sum_x", "sum_x2", "converged", "estimate")
+    out["batched_same_result"] = all(all(a[k] == b[k] for k in keys) for a, b in zip(plain, batched))
+    if served is not None:
+        out["served_same_result"] = all(all(a[k] == b[k] for k in keys) for a, b in zip(plain, served))
+    trials = sum(r["trials"] for r in plain)
+    out.update({"trials": int(trials), "converged": int(sum(r["converged"] for r in plain)),
+                "plain_samples_per_s": trials / out["plain_s"], "batched_samples_per_s": trials / out["batched_s"],
+                "batched_speedup": out["plain_s"] / out["batched_s"],
+                "plain_launches": int(sum(r["launches"] for r in plain)),
+                "batched_epochs": int(max(r["launches"] for r in batched))})
+    out["per_query"] = [{"pattern": name, "budget": b, "trials": int(r["trials"]), "converged": int(r["converged"]),
+                         "eps_hat": r["eps_hat"], "plain_s": r["s"]}
+                        for (name, _, b), r in zip(qs, plain)]
     info = g.info()
+    out["graph"] = (f"R-MAT scale {scale} (device), nv {info['nv']}, nnz {info['nnz']}, "
+                    f"max degree {info['max_degree']}")
     g.close()
-    return {"graph": f"R-MAT scale {scale} (device), nv {info['nv']}, nnz {info['nnz']}, max degree {info['max_degree']}",
-            "generate_s": t_gen, "preprocess_s": t_prep, "tables_s": t_tables, "queries": len(qs),
-            "trials": total, "autotuned_ctas_per_sm": best, "autotuned_tiles_per_item": span, "plain_s": t_plain, "batched_s": t_batch,
-            "plain_samples_per_s": total / t_plain, "batched_samples_per_s": total / t_batch,
-            "same_results": same}
+    torch.cuda.empty_cache()
+    return out
 
 
 # ------------------------------------------------------------------ large graph
@@ -649,6 +796,92 @@ def anchor_vs_exact(agis, g, names, cap_log2=30):
 
 # ------------------------------------------------------------------ GPU arm
 
+def random_access_gbs(agis, stream, local):
+    """Random 32-byte-sector read bandwidth over 16 GB (far beyond L2): the random-
+    access roofline of the sampler's dependent gathers and searches."""
+    import torch
+    try:
+        buf = torch.empty(16 << 30, dtype=torch.uint8, device="cuda")
+        sink = torch.zeros(1, dtype=torch.int64, device="cuda")
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        threads = sms * 2048
+        reads = 1 << 30
+        per = -(-reads // threads)
+        per = -(-per // 8) * 8
+        issued = threads * per
+        best = None
+        for rep in range(4):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            agis.probe_random_read(buf.data_ptr(), buf.numel(), reads, rep + 1, stream.cuda_stream, sink.data_ptr())
+            b.record(stream)
+            b.synchronize()
+            ms_r = a.elapsed_time(b)
+            if rep > 0 and (best is None or ms_r < best):
+                best = ms_r
+        del buf
+        torch.cuda.empty_cache()
+        return issued * 32 / (best / 1000.0) / 1e9
+    except Exception:
+        return None
+
+
+def time_to_1pct(agis, g, pats, names, args, deadline):
+    """Time to +-1% at 95% confidence (Alg. 1) for the benchmark patterns: one plain
+    call per pattern, one batched call, one server with all of them submitted at
+    once (identical results required), then f_uniform plain calls for contrast."""
+    chunk = 1 << args.tte_chunk_log2
+    acc = dict(eps=0.01, delta=0.05, chunk_trials=chunk, min_trials=chunk)
+    cap = 1 << args.tte_cap_log2
+    out = {"chunk_trials": chunk, "cap_trials": cap}
+    keys = ("trials", "hits", "sum_x", "sum_x2", "converged", "estimate")
+    opts = [agis.default_opts(mode=0, seed=101 + i, max_trials=cap, **acc) for i in range(len(pats))]
+    plain = []
+    t0 = time.perf_counter()
+    for i, (p, o) in enumerate(zip(pats, opts)):
+        t1 = time.perf_counter()
+        r = agis.estimate(g, p, o)
+        r["s"] = time.perf_counter() - t1
+        plain.append(r)
+    out["plain_total_s"] = time.perf_counter() - t0
+    out["plain"] = [{"pattern": n, "s": r["s"], "trials": int(r["trials"]), "converged": int(r["converged"]),
+                     "launches": int(r["launches"]), "estimate": r["estimate"], "eps_hat": r["eps_hat"]}
+                    for n, r in zip(names, plain)]
+    t0 = time.perf_counter()
+    br = agis.estimate_batch(g, pats, opts)
+    out["batched_total_s"] = time.perf_counter() - t0
+    out["batched_same_result"] = all(all(a[k] == b[k] for k in keys) for a, b in zip(plain, br))
+    srv = agis.Server(g, 200 << 30, 64)
+    t0 = time.perf_counter()
+    tickets = [srv.submit(p, o) for p, o in zip(pats, opts)]
+    done = {}
+    while len(done) < len(tickets):
+        for tk in tickets:
+            if tk not in done:
+                r = srv.poll(tk)
+                if r is not None:
+                    done[tk] = r
+        time.sleep(0.0002)
+    out["served_total_s"] = time.perf_counter() - t0
+    out["served_same_result"] = all(all(done[tk][k] == a[k] for k in keys) for tk, a in zip(tickets, plain))
+    srv.close()
+    uni = []
+    ucap = 1 << args.uniform_cap_log2
+    for i, p in enumerate(pats):
+        if time.perf_counter() + ucap / RATE_FLOOR["bench"] > deadline:
+            uni.append({"pattern": names[i], "skipped": "deadline"})
+            continue
+        o = agis.default_opts(mode=2, seed=101 + i, max_trials=ucap, **acc)
+        t1 = time.perf_counter()
+        r = agis.estimate(g, p, o)
+        need = r["trials"] if r["converged"] else int(r["trials"] * (r["eps_hat"] / 0.01) ** 2)
+        uni.append({"pattern": names[i], "s": time.perf_counter() - t1, "trials": int(r["trials"]),
+                    "converged": int(r["converged"]), "trials_needed": need, "eps_hat": r["eps_hat"]})
+    out["uniform_plain"] = uni
+    return out
+
+
 def run_gpu(args, world, rank, local):
     import torch
     from paper_2601_01388_b300 import build
@@ -656,9 +889,12 @@ def run_gpu(args, world, rank, local):
     from paper_2601_01388_b300 import agis
     from paper_2601_01388_b300 import inputs as I
 
+    t_start = time.perf_counter()
+    deadline = t_start + args.deadline_s
     names = [n for n in args.patterns.split(",") if n]
     trials = 1 << args.log2_trials
     ntiles = (trials + agis.TILE - 1) // agis.TILE
+    warm_trials = min(trials, 1 << args.warmup_log2_trials)
     off, cols, t_gen = make_workload(args.scale)
 
     pool = None
@@ -669,39 +905,39 @@ def run_gpu(args, world, rank, local):
     torch.cuda.set_device(local)
     stream = torch.cuda.Stream()
     ctx = agis.Context(local, stream.cuda_stream)
+    skipped = {}
     with torch.cuda.stream(stream):
         g = agis.Graph(ctx, off, cols, validate=True)
         info = g.info()
         pats = [agis.Pattern(*I.PATTERNS[n]) for n in names]
         opts = [agis.default_opts(mode=0, seed=1 + i, eps=0.0, max_trials=trials) for i in range(len(names))]
-        outs = [torch.zeros(ntiles * 4, dtype=torch.int64, device="cuda") for _ in names]
+        out = torch.zeros(ntiles * agis.TILE_WORDS, dtype=torch.int64, device="cuda")
 
-        def step(record):
-            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3 + 2 * len(names))]
+        def step(j, n_trials):
+            """Step j: the whole path for pattern j mod P (a plain per-query launch)."""
+            i = j % len(names)
+            nt = (n_trials + agis.TILE - 1) // agis.TILE
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
             ev[0].record(stream)
             g.preprocess(1, CMIN)                           # a1, a2 (Sec. 4.4)
             ev[1].record(stream)
-            for p, o in zip(pats, opts):                    # a3, a4 (tables + prefix sums)
-                agis.prepare(g, p, o)
+            agis.prepare(g, pats[i], opts[i])               # a3, a4 (tables + prefix sums)
             ev[2].record(stream)
-            for j, (p, o) in enumerate(zip(pats, opts)):    # a5..a10 (Alg. 3 + reductions)
-                ev[3 + 2 * j].record(stream)
-                agis.sample_device(g, p, o, 0, ntiles, outs[j].data_ptr())
-                ev[4 + 2 * j].record(stream)
-            words = [o.cpu().numpy().view(np.uint64) for o in outs]   # step result to host
+            agis.sample_device(g, pats[i], opts[i], 0, nt, out.data_ptr())   # a5..a10
+            ev[3].record(stream)
+            words = out[:nt * agis.TILE_WORDS].cpu().numpy().view(np.uint64)  # step result to host
+            ev[4].record(stream)
             stream.synchronize()
-            res = []
-            for w in words:
-                h, sec, sx, sx2 = agis.tile_sums(w)
-                res.append((int(h.sum()), int(sec.sum()), float(sx.sum()), float(sx2.sum())))
-            t = {"preprocess": ev[0].elapsed_time(ev[1]), "tables": ev[1].elapsed_time(ev[2]),
-                 "sample": [ev[3 + 2 * j].elapsed_time(ev[4 + 2 * j]) for j in range(len(names))]}
-            if record is not None:
-                record.append((t, res))
-            return t, res
+            s = agis.tile_sums(words)
+            return {"pattern": i, "trials": n_trials, "preprocess": ev[0].elapsed_time(ev[1]),
+                    "tables": ev[1].elapsed_time(ev[2]), "sample": ev[2].elapsed_time(ev[3]),
+                    "readback": ev[3].elapsed_time(ev[4]), "hits": int(s["hits"].sum()),
+                    "sectors": int(s["sectors"].sum()), "streamed": int(s["streamed"].sum()),
+                    "survey": int(s["survey"].sum()), "sum_x": float(s["sum_x"].sum()),
+                    "sum_x2": float(s["sum_x2"].sum())}
 
-        for _ in range(args.warmup):
-            step(None)
+        for j in range(args.warmup):
+            step(j, warm_trials)
         stream.synchronize()
         barrier(world)
         torch.cuda.synchronize()
@@ -712,8 +948,8 @@ def run_gpu(args, world, rank, local):
         e1 = torch.cuda.Event(enable_timing=True)
         recs = []
         e0.record(stream)
-        for _ in range(args.steps):
-            step(recs)
+        for j in range(args.steps):
+            recs.append(step(j, trials))
         e1.record(stream)
         stream.synchronize()
         torch.cuda.synchronize()
@@ -722,153 +958,114 @@ def run_gpu(args, world, rank, local):
         clk = clocks.stop()
         ms = e0.elapsed_time(e1) / args.steps
         ms = allreduce_max(ms, world)
-        trials_per_step = trials * len(names)
-        value = trials_per_step * world / (ms / 1000.0)
+        value = trials * world / (ms / 1000.0)
+        t_timed_end = time.perf_counter()
 
-        # random 32-byte-sector read bandwidth over 16 GB (the random-access roofline)
-        rand_gbs = None
-        try:
-            buf = torch.empty(16 << 30, dtype=torch.uint8, device="cuda")
-            sink = torch.zeros(1, dtype=torch.int64, device="cuda")
-            sms = torch.cuda.get_device_properties(local).multi_processor_count
-            threads = sms * 2048
-            reads = 1 << 30
-            per = -(-reads // threads)
-            per = -(-per // 8) * 8
-            issued = threads * per
-            best = None
-            for rep in range(4):
-                a = torch.cuda.Event(enable_timing=True)
-                b = torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                agis.probe_random_read(buf.data_ptr(), buf.numel(), reads, rep + 1, stream.cuda_stream, sink.data_ptr())
-                b.record(stream)
-                b.synchronize()
-                ms_r = a.elapsed_time(b)
-                if rep > 0 and (best is None or ms_r < best):
-                    best = ms_r
-            rand_gbs = issued * 32 / (best / 1000.0) / 1e9
-            del buf
-            torch.cuda.empty_cache()
-        except Exception:
-            rand_gbs = None
+        rand_gbs = random_access_gbs(agis, stream, local)
 
-        # roofline of the sampler kernel: algorithmic sectors / its own event time
-        samp_ms = [sum(t["sample"]) for t, _ in recs]
-        sectors = [sum(r[1] for r in res) for _, res in recs]
-        per_launch_ms = statistics.mean([x for t, _ in recs for x in t["sample"]])
-        achieved = statistics.mean([s * 32 / (m / 1000.0) for s, m in zip(sectors, samp_ms)]) / 1e9
+        # roofline of the sampler kernel (the dominant launch): algorithmic sectors
+        # counted by the kernel itself / its own event time, per launch
         peak, peak_kind = measured_peaks()
-        traffic = profile_traffic(trials)
-        last = recs[-1][1]
-        phases = {k: statistics.mean([t[k] for t, _ in recs]) for k in ("preprocess", "tables")}
-        phases["sample"] = statistics.mean(samp_ms)
-        per_pattern = {n: {"estimate": r[2] / trials, "hits": r[0], "sectors_per_trial": r[1] / trials,
-                           "ms": statistics.mean([t["sample"][j] for t, _ in recs])}
-                       for j, (n, r) in enumerate(zip(names, last))}
+        per_launch_ms = statistics.mean([r["sample"] for r in recs])
+        alg_bytes = statistics.mean([r["sectors"] * 32 for r in recs])
+        achieved = statistics.mean([r["sectors"] * 32 / (r["sample"] / 1000.0) for r in recs]) / 1e9
+        dram = profile_traffic()
+        traffic = None
+        if dram and all(names[r["pattern"]] in dram for r in recs):
+            traffic = statistics.mean([dram[names[r["pattern"]]] * r["trials"] for r in recs])
+        # time bound of the byte mix: streamed sectors at the copy peak, the rest at
+        # the random-sector rate; frac_time = that bound / the measured kernel time
+        model = None
+        if rand_gbs:
+            bounds = [(r["streamed"] * 32 / (peak * 1e9) + (r["sectors"] - r["streamed"]) * 32 / (rand_gbs * 1e9),
+                       r["sample"] / 1000.0) for r in recs]
+            model = {"streamed_sectors_per_trial": statistics.mean([r["streamed"] / r["trials"] for r in recs]),
+                     "random_sectors_per_trial": statistics.mean([(r["sectors"] - r["streamed"]) / r["trials"]
+                                                                  for r in recs]),
+                     "bound_ms_per_launch": 1000.0 * statistics.mean([b for b, _ in bounds]),
+                     "frac_time": sum(b for b, _ in bounds) / sum(t for _, t in bounds)}
+        phases = {k: statistics.mean([r[k] for r in recs]) for k in ("preprocess", "tables", "sample", "readback")}
+        per_pattern = {}
+        for i, n in enumerate(names):
+            rs = [r for r in recs if r["pattern"] == i]
+            if not rs:
+                continue
+            tr = sum(r["trials"] for r in rs)
+            per_pattern[n] = {"steps": len(rs), "estimate": rs[-1]["sum_x"] / rs[-1]["trials"],
+                              "hits": rs[-1]["hits"], "sample_ms": statistics.mean([r["sample"] for r in rs]),
+                              "step_ms": statistics.mean([r["preprocess"] + r["tables"] + r["sample"] + r["readback"]
+                                                          for r in rs]),
+                              "samples_per_s": tr / (sum(r["sample"] for r in rs) / 1000.0),
+                              "sectors_per_trial": sum(r["sectors"] for r in rs) / tr,
+                              "streamed_sectors_per_trial": sum(r["streamed"] for r in rs) / tr,
+                              "survey_sectors_per_trial": sum(r["survey"] for r in rs) / tr,
+                              "algorithmic_gbs": sum(r["sectors"] * 32 for r in rs) /
+                                                 (sum(r["sample"] for r in rs) / 1000.0) / 1e9,
+                              "dram_bytes_per_trial": dram.get(n) if dram else None}
+        survey_gbs = statistics.mean([r["survey"] * 32 / (r["sample"] / 1000.0) for r in recs]) / 1e9
 
-        # ---- end to end through the C ABI from pinned host buffers
+        # ---- end to end through the C ABI from pinned host buffers: every step uploads
+        # the graph, preprocesses it, builds the pattern's tables, runs the estimate call
+        # (its per-tile sums come back to the host) and returns the result
         e2e = None
         if not args.no_e2e:
-            h_off = torch.from_numpy(off).pin_memory().numpy()
-            h_cols = torch.from_numpy(cols).pin_memory().numpy()
-            reps = 1
-            d2h = 0
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            for _ in range(reps):
-                ge = agis.Graph(ctx, h_off, h_cols, validate=False)
-                ge.preprocess(1, CMIN)
-                for p, o in zip(pats, opts):
-                    r = agis.estimate(ge, p, o)
-                    d2h += ntiles * 32 + 136
-                ge.close()
-            torch.cuda.synchronize()
-            dt = (time.perf_counter() - t0) / reps
-            e2e = {"value": trials_per_step / dt, "unit": "samples/s",
-                   "h2d_bytes_per_step": int(h_off.nbytes + h_cols.nbytes + len(names) * 600),
-                   "d2h_bytes_per_step": int(d2h / reps), "s_per_step": dt}
+            n_e2e = args.e2e_steps or len(names)
+            per_s = statistics.mean([r["preprocess"] + r["tables"] + r["sample"] + r["readback"] for r in recs]) / 1000
+            if time.perf_counter() + n_e2e * per_s * 1.2 > deadline:
+                n_e2e = max(0, int((deadline - time.perf_counter()) / (per_s * 1.2)))
+            if n_e2e > 0:
+                h_off = torch.from_numpy(off).pin_memory()
+                h_cols = torch.from_numpy(cols).pin_memory()
+                ho, hc = h_off.numpy(), h_cols.numpy()
+                d2h, h2d = 0, 0
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                for j in range(n_e2e):
+                    i = j % len(names)
+                    ge = agis.Graph(ctx, ho, hc, validate=False)
+                    ge.preprocess(1, CMIN)
+                    r = agis.estimate(ge, pats[i], opts[i])
+                    ge.close()
+                    h2d += ho.nbytes + hc.nbytes + ctypes.sizeof(agis.Opts)
+                    d2h += ntiles * agis.TILE_WORDS * 8
+                torch.cuda.synchronize()
+                dt = time.perf_counter() - t0
+                e2e = {"value": n_e2e * trials / dt, "unit": "samples/s", "h2d_bytes_per_step": int(h2d / n_e2e),
+                       "d2h_bytes_per_step": int(d2h / n_e2e), "steps": n_e2e, "s_per_step": dt / n_e2e}
+            else:
+                skipped["e2e"] = "deadline"
 
-        # ---- time to +-1% (95% CI): plain, batched, served; and f_uniform for contrast
         tte = None
         if not args.no_tte:
-            tte = {}
-            acc = dict(eps=0.01, delta=0.05, chunk_trials=1 << 16, min_trials=1 << 16)
-            plain = []
-            t0 = time.perf_counter()
-            for i, p in enumerate(pats):
-                o = agis.default_opts(mode=0, seed=101 + i, max_trials=1 << 34, **acc)
-                t1 = time.perf_counter()
-                r = agis.estimate(g, p, o)
-                plain.append({"pattern": names[i], "s": time.perf_counter() - t1, "trials": r["trials"],
-                              "converged": r["converged"], "estimate": r["estimate"]})
-            tte["plain_total_s"] = time.perf_counter() - t0
-            tte["plain"] = plain
-            bo = [agis.default_opts(mode=0, seed=101 + i, max_trials=1 << 34, **acc) for i in range(len(pats))]
-            t0 = time.perf_counter()
-            br = agis.estimate_batch(g, pats, bo)
-            tte["batched_total_s"] = time.perf_counter() - t0
-            tte["batched_same_result"] = all(a["trials"] == b["trials"] and a["estimate"] == b["estimate"]
-                                             for a, b in zip(plain, br))
-            srv = agis.Server(g, 200 << 30, 64)
-            t0 = time.perf_counter()
-            tickets = [srv.submit(p, o) for p, o in zip(pats, bo)]
-            done = {}
-            while len(done) < len(tickets):
-                for tk in tickets:
-                    if tk not in done:
-                        r = srv.poll(tk)
-                        if r is not None:
-                            done[tk] = r
-                time.sleep(0.0005)
-            tte["served_total_s"] = time.perf_counter() - t0
-            tte["served_same_result"] = all(done[tk]["trials"] == a["trials"] for tk, a in zip(tickets, plain))
-            srv.close()
-            uni = []
-            for i, p in enumerate(pats):
-                o = agis.default_opts(mode=2, seed=101 + i, max_trials=1 << 30, **acc)
-                t1 = time.perf_counter()
-                r = agis.estimate(g, p, o)
-                uni.append({"pattern": names[i], "s": time.perf_counter() - t1, "trials": r["trials"],
-                            "converged": r["converged"]})
-            tte["uniform_plain"] = uni
-
-        large = None
-        if args.large:
-            large = large_graph(agis, ctx, args.large_scale)
+            tte = time_to_1pct(agis, g, pats, names, args, deadline)
 
         batching = None
         if args.batch64:
-            batching = batch64(agis, ctx, args.batch_scale, stream)
+            plan = plan_seconds(args)["batch64"]
+            if time.perf_counter() + plan * 0.5 > deadline:
+                skipped["batch64"] = "deadline"
+            else:
+                batching = batch64(agis, ctx, args.batch_scale, eps=args.batch_eps, chunk_log2=args.tte_chunk_log2,
+                                   deadline=deadline)
 
-        serving = None
-        if args.serve:
-            serving = serving_configs(agis, ctx, args.serve_seconds)
-
-        abl = None
-        if args.ablation:
-            abl = ablation(agis, g)
-
-        conc = None
-        if args.concentration:
-            conc = concentration_run(agis, g)
-
-        dag = None
-        if args.dag:
-            dag = cliques_oriented(agis, g)
-
-        anch = None
-        if args.anchor:
-            anch = anchor_vs_exact(agis, g, names + ["6-clique"])
+        large = large_graph(agis, ctx, args.large_scale) if args.large else None
+        serving = serving_configs(agis, ctx, args.serve_seconds) if args.serve else None
+        abl = ablation(agis, g) if args.ablation else None
+        conc = concentration_run(agis, g) if args.concentration else None
+        dag = cliques_oriented(agis, g) if args.dag else None
+        anch = anchor_vs_exact(agis, g, names + ["6-clique"]) if args.anchor else None
 
     cpu = None
     if pool is not None:
-        t_prep = pool.preprocess()
-        rate, n, dt, per = cpu_rate(pool, names, args.cpu_seconds)
-        cpu = {"value": rate, "unit": "samples/s", "cores": pool.procs, "kind": "oracle",
-               "sample": f"{per} trials of each of {', '.join(names)} (AUTO, seeds 1..4) on the same "
-                         f"scale-{args.scale} graph, split over {pool.procs} processes; {dt:.1f} s; "
-                         f"oracle preprocessing {t_prep:.1f} s not included"}
+        if time.perf_counter() + 4 * args.cpu_seconds > deadline + 200:
+            skipped["cpu_baseline"] = "deadline"
+        else:
+            t_prep = pool.preprocess()
+            rate, n, dt, per = cpu_rate(pool, names, args.cpu_seconds)
+            cpu = {"value": rate, "unit": "samples/s", "cores": pool.procs, "kind": "oracle",
+                   "sample": f"{per} trials of each of {', '.join(names)} (AUTO, seeds 1..4) on the same "
+                             f"scale-{args.scale} graph, split over {pool.procs} processes; {dt:.1f} s; "
+                             f"oracle preprocessing {t_prep:.1f} s not included"}
         pool.close()
 
     line = {
@@ -876,6 +1073,8 @@ def run_gpu(args, world, rank, local):
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": workload_name(args, names),
+                   "step": f"the full {trials}-trial query of one pattern (step j: pattern j mod {len(names)}), "
+                           f"preprocessing and tables included; warm-up steps at {warm_trials} trials",
                    "nv": info["nv"], "nnz": info["nnz"], "max_degree": info["max_degree"],
                    "trials_per_pattern": trials, "parallelism": f"replicas x{world}",
                    "l2": l2_note(off.nbytes + cols.nbytes),
@@ -883,9 +1082,10 @@ def run_gpu(args, world, rank, local):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "kernel": "sample_kernel",
                      "peak_kind": peak_kind, "per_launch_ms": per_launch_ms,
+                     "algorithmic_bytes_per_launch": alg_bytes,
+                     "survey_model_gbs": survey_gbs,
                      "random_access_gbs": rand_gbs,
-                     "frac_of_random_access": (achieved / rand_gbs) if rand_gbs else None,
-                     "algorithmic_bytes_per_launch": statistics.mean(sectors) * 32 / len(names)},
+                     "byte_mix_bound": model},
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": int(launches),
@@ -893,11 +1093,12 @@ def run_gpu(args, world, rank, local):
         "phases_ms": phases,
         "per_pattern": per_pattern,
         "time_to_1pct": tte,
+        "batch64": batching,
+        "timing": {"timed_loop_s": t_timed_end - t_start, "total_s": time.perf_counter() - t_start,
+                   "skipped": skipped},
     }
     if serving is not None:
         line["serving"] = serving
-    if batching is not None:
-        line["batch64"] = batching
     if large is not None:
         line["large_graph"] = large
     if abl is not None:
@@ -943,6 +1144,12 @@ def run_reference(args, world, rank):
 
 def main():
     args = parse_args()
+    if args.summarize_ncu:
+        names = [n for n in args.patterns.split(",") if n]
+        s = summarize_ncu(args.summarize_ncu, args.summary_out or TRAFFIC_SUMMARY, names, 1 << args.log2_trials,
+                          args.ncu_command, workload_name(args, names))
+        print(json.dumps(s["per_pattern"]))
+        return
     world, rank, local = dist_init()
     if args.impl == "reference":
         line = run_reference(args, world, rank)

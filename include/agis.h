@@ -85,6 +85,10 @@ typedef struct {
     int32_t reserved;       /* must be 0                                               */
 } agis_opts;
 
+/* Words of one tile's output in agis_sample_device: hits, sectors, the FP64 sum X
+ * and sum X^2 bit patterns, sectors_streamed, sectors_survey (see agis_result). */
+#define AGIS_TILE_WORDS 6
+
 typedef struct {
     double estimate;        /* mean sampler output = estimate of C(G,P) (embeddings)    */
     double subgraphs;       /* estimate / |Aut(P)|                                      */
@@ -93,11 +97,18 @@ typedef struct {
     double sum_x, sum_x2;   /* FP64 sums over the trials used                           */
     uint64_t trials;        /* trials used (a multiple of chunk_trials unless capped)   */
     uint64_t hits;          /* successful trajectories among them                       */
-    uint64_t sectors;       /* algorithmic 32-byte sectors of those trials (model)      */
+    uint64_t sectors;       /* algorithmic 32-byte sectors of those trials (the cost
+                               model: the sectors Alg. 3 must touch with no reuse)     */
     int32_t converged;      /* 1 if Alg. 1 accepted eps at a checkpoint                 */
     int32_t launches;       /* sampler kernel launches used                             */
     double t_prep_s;        /* weight-table builds done for this call                  */
     double t_sample_s;      /* wall time of the sampling loop                           */
+    uint64_t sectors_streamed; /* the part of `sectors` read as consecutive runs: scans
+                               of the shortest backward row and rows read once by a
+                               merge; the rest are random accesses                      */
+    uint64_t sectors_survey;   /* the plain count: one membership search per scanned
+                               entry in every other backward row, and weight reads on
+                               every step D(i) puts under f_approx                       */
 } agis_result;
 
 const char *agis_status_str(int status);
@@ -255,7 +266,8 @@ int agis_estimate_batch(agis_graph *g, int n, const agis_pattern *const *pattern
 /* agis_dump_trials: per-trial record of trials [first, first+count) of the query:
  * emb[count*8] int32 trajectory (step order; -1 after a failed step), hit[count]
  * (1 = the trajectory is an embedding), x[count] FP64 sampler output (Alg. 3:
- * 1/p or 0), sectors[count] algorithmic sectors.  Host arrays; any may be NULL.
+ * 1/p or 0), sectors[count*3] the trial's sector counts (sectors, sectors_streamed,
+ * sectors_survey as in agis_result).  Host arrays; any may be NULL.
  * Errors: ARG, STATE, NOMEM, CUDA. */
 int agis_dump_trials(agis_graph *g, const agis_pattern *p, const agis_opts *opts,
                      uint64_t first, uint64_t count, int32_t *emb, uint8_t *hit, double *x,
@@ -267,8 +279,9 @@ int agis_tile_trials(void);
 
 /* agis_sample_device: fixed-budget sampling with all buffers on the device:
  * trials [first, first + ntiles*T) of the query, T = agis_tile_trials(), per-tile sums written to
- * tile_out (device, ntiles * 4 uint64 words per tile: hits, sectors, then the FP64
- * sum X and sum X^2 bit patterns).  Enqueued on ctx's stream, no host sync.
+ * tile_out (device, AGIS_TILE_WORDS uint64 words per tile: hits, sectors, the FP64
+ * sum X and sum X^2 bit patterns, sectors_streamed, sectors_survey).  Enqueued on
+ * ctx's stream, no host sync.
  * Errors: ARG, STATE, NOMEM, CUDA. */
 int agis_sample_device(agis_graph *g, const agis_pattern *p, const agis_opts *opts,
                        uint64_t first, uint64_t ntiles, uint64_t *tile_out);
@@ -339,8 +352,12 @@ double agis_z_of_delta(double delta);
  * queries while a slot is free and their weight tables fit in scratch_bytes of
  * device memory, runs all admitted queries together in epochs (each epoch one
  * persistent launch over every admitted query's next tiles), retires queries at
- * their first converged checkpoint and admits waiting ones between epochs
- * (continuous batching).  Results equal agis_estimate's. */
+ * their first converged checkpoint and admits waiting ones as slots and memory
+ * free up (continuous batching).  Two epochs are in flight at a time: the next one
+ * is staged and enqueued while the current one runs, so queries that arrive while
+ * others are on the GPU join the next epoch and their work overlaps.  Results
+ * equal agis_estimate's.  The server allocates its own launch buffers and one
+ * candidate-list scratch (as large as an estimate call's) on the graph's device. */
 int agis_server_create(agis_graph *g, size_t scratch_bytes, int max_slots, agis_server **out);
 /* agis_server_submit: copies the pattern and options; *ticket identifies the query.
  * Errors: ARG, BUSY (more than 65536 queries waiting). */
@@ -348,10 +365,19 @@ int agis_server_submit(agis_server *s, const agis_pattern *p, const agis_opts *o
                        uint64_t *ticket);
 /* agis_server_poll: AGIS_OK and *out filled when done (the ticket is then
  * released), AGIS_ERR_BUSY while queued or running, ARG for an unknown ticket, or
- * the query's own error status.  latency_s (may be NULL) = completion - submit. */
-int agis_server_poll(agis_server *s, uint64_t ticket, agis_result *out, double *latency_s);
-/* agis_server_stats: queries completed, epochs launched, peak admitted slots. */
-int agis_server_stats(agis_server *s, uint64_t *completed, uint64_t *epochs, int32_t *peak_slots);
+ * the query's own error status.  latency_s (may be NULL) = completion - submit.
+ * epochs (may be NULL; 2 entries) = the index of the first epoch that ran tiles of
+ * this query and of the epoch whose sums finished it (epochs are numbered from 0
+ * in launch order): two queries whose ranges overlap shared the GPU. */
+int agis_server_poll(agis_server *s, uint64_t ticket, agis_result *out, double *latency_s,
+                     uint64_t *epochs);
+/* agis_server_stats: queries completed, epochs completed, peak admitted slots,
+ * gpu_busy_s = summed device time of the epochs (events around each launch) and
+ * busy_span_s = wall time during which at least one epoch was in flight; their
+ * ratio is the fraction of that time the GPU was not idle.  Any pointer may be
+ * NULL. */
+int agis_server_stats(agis_server *s, uint64_t *completed, uint64_t *epochs, int32_t *peak_slots,
+                      double *gpu_busy_s, double *busy_span_s);
 int agis_server_destroy(agis_server *s);
 
 #ifdef __cplusplus

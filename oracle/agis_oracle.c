@@ -617,8 +617,10 @@ static int closes_all(const orc_query *Q, int i, const int32_t *tau, int a, int3
 }
 
 /* Sector model of an anchor-draw step: the single-backward draw on the anchor row
- * plus, per other backward vertex, one offsets sector and one membership search. */
-static uint64_t anchor_sectors(const orc_query *Q, int i, const int32_t *tau, int a)
+ * plus, per other backward vertex, one offsets sector and one membership search.
+ * Every sector of it is a random access, and the survey's count is the same (an
+ * anchor step always reads its weights under f_approx). */
+static void anchor_sectors(const orc_query *Q, int i, const int32_t *tau, int a, uint64_t sec[3])
 {
     const orc_plan *p = &Q->plan;
     int32_t anchor = tau[p->back[i][a]];
@@ -631,7 +633,8 @@ static uint64_t anchor_sectors(const orc_query *Q, int i, const int32_t *tau, in
         int32_t u = tau[p->back[i][b]];
         s += 1 + sec_search(Q->off[u + 1] - Q->off[u], 4);
     }
-    return s;
+    sec[0] += s;
+    sec[2] += s;
 }
 
 /* Whether the cost model counts weight reads for step i.  A later step whose
@@ -649,7 +652,7 @@ static int weights_read(const orc_query *Q, int i)
 }
 
 /* Algorithmic-sector model of one step (a count of 32-byte sectors the step must
- * touch with no reuse; see the design notes):
+ * touch with no reuse; see the design notes), added into sec[0]:
  *   step 1: search over the (nv+1)-entry running-weight array (+1 for q(v_1));
  *   later : one sector per backward vertex's offsets; one backward edge: i-1
  *           trajectory-membership searches in the row, a running-weight search in
@@ -657,19 +660,30 @@ static int weights_read(const orc_query *Q, int i)
  *           several: a scan of the shortest backward row; for each other backward
  *           row the cheaper of reading it once (a merge) and one membership search
  *           per scanned entry; one q gather per candidate under f_approx
- *           (weights_read: none where the weights are equal on S_tau). */
-static uint64_t step_sectors(const orc_query *Q, int i, const int32_t *tau, int64_t nS)
+ *           (weights_read: none where the weights are equal on S_tau).
+ * sec[1] receives the streamed part of sec[0]: the scan of the shortest row and the
+ * other rows read once; every other sector is a random access (searches, offsets,
+ * gathers).  sec[2] receives the plain count of the method's reads with neither
+ * saving: one membership search per scanned entry in every other backward row, and
+ * the weight reads of every step that D(i) puts under f_approx, equal weights or
+ * not. */
+static void step_sectors(const orc_query *Q, int i, const int32_t *tau, int64_t nS, uint64_t sec[3])
 {
     const orc_plan *p = &Q->plan;
-    if (i == 0) return sec_search(Q->nv + 1, 8) + (Q->use_approx[0] ? 1u : 0u);
+    if (i == 0) {
+        uint64_t s = sec_search(Q->nv + 1, 8) + (Q->use_approx[0] ? 1u : 0u);
+        sec[0] += s;
+        sec[2] += s;
+        return;
+    }
     int nb = p->nback[i];
-    uint64_t s = (uint64_t)nb;
     if (nb == 1) {
         int64_t d = Q->off[tau[p->back[i][0]] + 1] - Q->off[tau[p->back[i][0]]];
-        s += (uint64_t)(i - 1) * sec_search(d, 4);
-        if (weights_read(Q, i)) s += sec_search(d, 8) + 1;
-        s += 1;
-        return s;
+        uint64_t s = 1 + (uint64_t)(i - 1) * sec_search(d, 4) + 1;
+        uint64_t w = sec_search(d, 8) + 1;
+        sec[0] += s + (weights_read(Q, i) ? w : 0);
+        sec[2] += s + (Q->use_approx[i] ? w : 0);
+        return;
     }
     int a = 0;
     int64_t da = -1;
@@ -678,36 +692,46 @@ static uint64_t step_sectors(const orc_query *Q, int i, const int32_t *tau, int6
         int64_t d = Q->off[v + 1] - Q->off[v];
         if (da < 0 || d < da) { da = d; a = b; }
     }
-    s += (uint64_t)((4 * da + 31) / 32);
+    uint64_t scan = (uint64_t)((4 * da + 31) / 32);
+    uint64_t s = (uint64_t)nb + scan, streamed = scan, survey = (uint64_t)nb + scan;
     for (int b = 0; b < nb; ++b) {
         if (b == a) continue;
         int32_t v = tau[p->back[i][b]];
         int64_t m = Q->off[v + 1] - Q->off[v];
         uint64_t read_once = (uint64_t)((4 * (m > 0 ? m : 1) + 31) / 32);
         uint64_t search_each = (uint64_t)da * sec_search(m, 4);
-        s += read_once < search_each ? read_once : search_each;
+        if (read_once < search_each) {
+            s += read_once;
+            streamed += read_once;
+        } else {
+            s += search_each;
+        }
+        survey += search_each;
     }
     if (weights_read(Q, i)) s += (uint64_t)nS;
-    return s;
+    if (Q->use_approx[i]) survey += (uint64_t)nS;
+    sec[0] += s;
+    sec[1] += streamed;
+    sec[2] += survey;
 }
 
 /* Alg. 3 for trial t: returns X = prod_i W_i / q_i (the inverse of the trajectory's
  * probability) on success and 0 when a candidate set is empty or has zero weight.
  * tau receives the sampled vertices (-1 past a failure). */
 double orc_trial(const orc_query *Q, uint64_t t, int32_t tau[ORC_MAXK], uint8_t *hit,
-                 uint64_t *sectors)
+                 uint64_t sectors[3])
 {
     const orc_plan *p = &Q->plan;
     for (int i = 0; i < ORC_MAXK; ++i) tau[i] = -1;
     double X = 1.0;
-    uint64_t sec = 0;
+    uint64_t sec[3] = {0, 0, 0};
     *hit = 0;
     for (int i = 0; i < p->k; ++i) {
         uint64_t W, q;
         int32_t v;
         if (i == 0) {
             W = Q->W1;
-            if (W == 0) { X = 0.0; sec += step_sectors(Q, i, tau, 0); goto done; }
+            if (W == 0) { X = 0.0; step_sectors(Q, i, tau, 0, sec); goto done; }
             uint64_t r = orc_draw_below(W, t, 1, ORC_STREAM_TRIAL, Q->seed);
             int64_t lo = 0, hi = Q->nv - 1;          /* first v with cum1[v] > r */
             while (lo < hi) {
@@ -716,11 +740,11 @@ double orc_trial(const orc_query *Q, uint64_t t, int32_t tau[ORC_MAXK], uint8_t 
             }
             v = (int32_t)lo;
             q = step_weight(Q, 0, v);
-            sec += step_sectors(Q, i, tau, 0);
+            step_sectors(Q, i, tau, 0, sec);
         } else if (Q->anchor && p->nback[i] >= 2) {
             int64_t n;
             int a = anchor_candidates(Q, i, tau, &W, &n);
-            sec += anchor_sectors(Q, i, tau, a);
+            anchor_sectors(Q, i, tau, a, sec);
             if (n == 0 || W == 0) { X = 0.0; goto done; }
             uint64_t r = orc_draw_below(W, t, (uint64_t)(i + 1), ORC_STREAM_TRIAL, Q->seed);
             uint64_t run = 0;
@@ -734,7 +758,7 @@ double orc_trial(const orc_query *Q, uint64_t t, int32_t tau[ORC_MAXK], uint8_t 
             if (!closes_all(Q, i, tau, a, v)) { X = 0.0; goto done; }
         } else {
             int64_t n = build_candidates(Q, i, tau, &W);
-            sec += step_sectors(Q, i, tau, n);
+            step_sectors(Q, i, tau, n, sec);
             if (n == 0 || W == 0) { X = 0.0; goto done; }
             uint64_t r = orc_draw_below(W, t, (uint64_t)(i + 1), ORC_STREAM_TRIAL, Q->seed);
             uint64_t run = 0;
@@ -751,42 +775,45 @@ double orc_trial(const orc_query *Q, uint64_t t, int32_t tau[ORC_MAXK], uint8_t 
     }
     *hit = 1;
 done:
-    *sectors = sec;
+    for (int j = 0; j < 3; ++j) sectors[j] = sec[j];
     return X;
 }
 
-/* Per-trial dump over trials [first, first+count). */
+/* Per-trial dump over trials [first, first+count); sectors: 3 words per trial. */
 void orc_trials(const orc_query *Q, uint64_t first, uint64_t count, int32_t *emb,
                 uint8_t *hit, double *x, uint64_t *sectors)
 {
     for (uint64_t c = 0; c < count; ++c) {
         int32_t tau[ORC_MAXK];
         uint8_t h;
-        uint64_t s;
-        double X = orc_trial(Q, first + c, tau, &h, &s);
+        uint64_t s[3];
+        double X = orc_trial(Q, first + c, tau, &h, s);
         if (emb) memcpy(emb + 8 * c, tau, sizeof(tau));
         if (hit) hit[c] = h;
         if (x) x[c] = X;
-        if (sectors) sectors[c] = s;
+        if (sectors) for (int j = 0; j < 3; ++j) sectors[3 * c + j] = s[j];
     }
 }
 
-/* Sums over trials [first, first+count): n, hits, sum X, sum X^2, sectors. */
+/* Sums over trials [first, first+count): n, hits, sum X, sum X^2, and the three
+ * sector counts. */
 void orc_sums(const orc_query *Q, uint64_t first, uint64_t count, uint64_t *hits,
-              double *sx, double *sx2, uint64_t *sectors)
+              double *sx, double *sx2, uint64_t sectors[3])
 {
-    uint64_t h = 0, sec = 0;
+    uint64_t h = 0, sec[3] = {0, 0, 0};
     double a = 0.0, b = 0.0;
     for (uint64_t c = 0; c < count; ++c) {
         int32_t tau[ORC_MAXK];
         uint8_t hh;
-        uint64_t s;
-        double X = orc_trial(Q, first + c, tau, &hh, &s);
-        h += hh; sec += s;
+        uint64_t s[3];
+        double X = orc_trial(Q, first + c, tau, &hh, s);
+        h += hh;
+        for (int j = 0; j < 3; ++j) sec[j] += s[j];
         a += X;
         b += X * X;
     }
-    *hits = h; *sx = a; *sx2 = b; *sectors = sec;
+    *hits = h; *sx = a; *sx2 = b;
+    for (int j = 0; j < 3; ++j) sectors[j] = sec[j];
 }
 
 /* ------------------------------------------------------------------------ */
@@ -808,6 +835,7 @@ typedef struct {
     uint64_t trials, hits, sectors;
     double sum_x, sum_x2, mean, var, eps_hat;
     int32_t converged;
+    uint64_t sectors_streamed, sectors_survey;
 } orc_estimate_result;
 
 static void alg1(double n, double sx, double sx2, double z, double *mu, double *var, double *eps_hat)
@@ -824,7 +852,7 @@ void orc_estimate(const orc_query *Q, double eps, double delta, uint64_t chunk,
                   uint64_t min_trials, uint64_t max_trials, orc_estimate_result *res)
 {
     double z = orc_z_of_delta(delta);
-    uint64_t n = 0, h = 0, sec = 0;
+    uint64_t n = 0, h = 0, sec[3] = {0, 0, 0};
     double sx = 0.0, sx2 = 0.0, mu = 0.0, var = 0.0, eh = INFINITY;
     int conv = 0;
     while (n < max_trials) {
@@ -833,9 +861,10 @@ void orc_estimate(const orc_query *Q, double eps, double delta, uint64_t chunk,
         for (uint64_t j = 0; j < c; ++j) {
             int32_t tau[ORC_MAXK];
             uint8_t hh;
-            uint64_t s;
-            double X = orc_trial(Q, n + j, tau, &hh, &s);
-            h += hh; sec += s;
+            uint64_t s[3];
+            double X = orc_trial(Q, n + j, tau, &hh, s);
+            h += hh;
+            for (int w = 0; w < 3; ++w) sec[w] += s[w];
             sx += X;
             sx2 += X * X;
         }
@@ -843,7 +872,8 @@ void orc_estimate(const orc_query *Q, double eps, double delta, uint64_t chunk,
         alg1((double)n, sx, sx2, z, &mu, &var, &eh);
         if (n >= min_trials && mu > 0.0 && eh <= eps) { conv = 1; break; }
     }
-    res->trials = n; res->hits = h; res->sectors = sec;
+    res->trials = n; res->hits = h; res->sectors = sec[0];
+    res->sectors_streamed = sec[1]; res->sectors_survey = sec[2];
     res->sum_x = sx; res->sum_x2 = sx2;
     res->mean = mu; res->var = var; res->eps_hat = eh; res->converged = conv;
 }

@@ -41,7 +41,8 @@ class Plan(C.Structure):
 class EstimateResult(C.Structure):
     _fields_ = [("trials", C.c_uint64), ("hits", C.c_uint64), ("sectors", C.c_uint64),
                 ("sum_x", C.c_double), ("sum_x2", C.c_double), ("mean", C.c_double),
-                ("var", C.c_double), ("eps_hat", C.c_double), ("converged", C.c_int32)]
+                ("var", C.c_double), ("eps_hat", C.c_double), ("converged", C.c_int32),
+                ("sectors_streamed", C.c_uint64), ("sectors_survey", C.c_uint64)]
 
 
 _lib = None
@@ -93,7 +94,7 @@ def lib():
         L.orc_trials.argtypes = [C.c_void_p, C.c_uint64, C.c_uint64, C.c_void_p, C.c_void_p,
                                  C.c_void_p, C.c_void_p]
         L.orc_sums.argtypes = [C.c_void_p, C.c_uint64, C.c_uint64, P(C.c_uint64),
-                               P(C.c_double), P(C.c_double), P(C.c_uint64)]
+                               P(C.c_double), P(C.c_double), C.c_void_p]
         L.orc_z_of_delta.argtypes = [C.c_double]
         L.orc_z_of_delta.restype = C.c_double
         L.orc_estimate.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_uint64, C.c_uint64,
@@ -289,16 +290,17 @@ class Query:
         emb = np.zeros((count, MAXK), dtype=np.int32)
         hit = np.zeros(count, dtype=np.uint8)
         x = np.zeros(count, dtype=np.float64)
-        sec = np.zeros(count, dtype=np.uint64)
+        sec = np.zeros((count, 3), dtype=np.uint64)     # model total, its streamed part, survey count
         lib().orc_trials(self._h, first, count, _ptr(emb), _ptr(hit), _ptr(x), _ptr(sec))
         return emb, hit, x, sec
 
     def sums(self, first, count):
-        h, sec = C.c_uint64(), C.c_uint64()
+        h = C.c_uint64()
+        sec = (C.c_uint64 * 3)()
         sx, sx2 = C.c_double(), C.c_double()
-        lib().orc_sums(self._h, first, count, C.byref(h), C.byref(sx), C.byref(sx2), C.byref(sec))
+        lib().orc_sums(self._h, first, count, C.byref(h), C.byref(sx), C.byref(sx2), sec)
         return {"trials": count, "hits": h.value, "sum_x": sx.value, "sum_x2": sx2.value,
-                "sectors": sec.value}
+                "sectors": sec[0], "sectors_streamed": sec[1], "sectors_survey": sec[2]}
 
     def estimate(self, eps=0.01, delta=0.05, chunk=1 << 16, min_trials=1 << 16,
                  max_trials=1 << 30):

@@ -48,7 +48,8 @@ class Result(C.Structure):
                 ("var", C.c_double), ("eps_hat", C.c_double), ("sum_x", C.c_double),
                 ("sum_x2", C.c_double), ("trials", C.c_uint64), ("hits", C.c_uint64),
                 ("sectors", C.c_uint64), ("converged", C.c_int32), ("launches", C.c_int32),
-                ("t_prep_s", C.c_double), ("t_sample_s", C.c_double)]
+                ("t_prep_s", C.c_double), ("t_sample_s", C.c_double),
+                ("sectors_streamed", C.c_uint64), ("sectors_survey", C.c_uint64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -94,8 +95,8 @@ _sig = {
     "agis_step_timers": ([VP, C.c_int], C.c_int),
     "agis_server_create": ([VP, C.c_size_t, C.c_int, P(VP)], C.c_int),
     "agis_server_submit": ([VP, VP, P(Opts), P(C.c_uint64)], C.c_int),
-    "agis_server_poll": ([VP, C.c_uint64, P(Result), P(C.c_double)], C.c_int),
-    "agis_server_stats": ([VP, P(C.c_uint64), P(C.c_uint64), P(C.c_int32)], C.c_int),
+    "agis_server_poll": ([VP, C.c_uint64, P(Result), P(C.c_double), P(C.c_uint64)], C.c_int),
+    "agis_server_stats": ([VP, P(C.c_uint64), P(C.c_uint64), P(C.c_int32), P(C.c_double), P(C.c_double)], C.c_int),
     "agis_server_destroy": ([VP], C.c_int),
 }
 for _name, (_args, _res) in _sig.items():
@@ -107,6 +108,7 @@ for _name, (_args, _res) in _sig.items():
 
 
 TILE = int(_lib.agis_tile_trials())    # trials per tile (the build's tile size)
+TILE_WORDS = 6                         # AGIS_TILE_WORDS: uint64 words of one tile's output
 
 
 class AgisError(RuntimeError):
@@ -372,7 +374,7 @@ def dump_trials(graph: Graph, pattern: Pattern, opts: Opts, first: int, count: i
     emb = np.zeros((count, 8), dtype=np.int32)
     hit = np.zeros(count, dtype=np.uint8)
     x = np.zeros(count, dtype=np.float64)
-    sec = np.zeros(count, dtype=np.uint64)
+    sec = np.zeros((count, 3), dtype=np.uint64)    # sectors, sectors_streamed, sectors_survey
     _check(_lib.agis_dump_trials(graph.h, pattern.h, C.byref(opts), first, count, _ptr(emb), _ptr(hit),
                                  _ptr(x), _ptr(sec)), "agis_dump_trials")
     return emb, hit, x, sec
@@ -395,15 +397,17 @@ def prepare(graph: Graph, pattern: Pattern, opts: Opts):
 
 def sample_device(graph: Graph, pattern: Pattern, opts: Opts, first: int, ntiles: int, tile_out_ptr: int):
     """Enqueues fixed-budget sampling; tile_out_ptr is a device address of
-    ntiles*4 uint64 words (e.g. a torch.uint64/int64 CUDA tensor's data_ptr())."""
+    ntiles*TILE_WORDS uint64 words (e.g. a torch.int64 CUDA tensor's data_ptr())."""
     _check(_lib.agis_sample_device(graph.h, pattern.h, C.byref(opts), first, ntiles, C.c_void_p(tile_out_ptr)),
            "agis_sample_device")
 
 
-def tile_sums(words: np.ndarray):
-    """Decodes tile output words (n x 4 uint64) into hits, sectors, sum X, sum X^2."""
-    w = np.ascontiguousarray(words, dtype=np.uint64).reshape(-1, 4)
-    return w[:, 0], w[:, 1], w[:, 2].view(np.float64), w[:, 3].view(np.float64)
+def tile_sums(words: np.ndarray) -> dict:
+    """Decodes tile output words (n x TILE_WORDS uint64): per-tile hits, sectors,
+    sum_x, sum_x2, streamed (sectors_streamed) and survey (sectors_survey)."""
+    w = np.ascontiguousarray(words, dtype=np.uint64).reshape(-1, TILE_WORDS)
+    return {"hits": w[:, 0], "sectors": w[:, 1], "sum_x": w[:, 2].view(np.float64),
+            "sum_x2": w[:, 3].view(np.float64), "streamed": w[:, 4], "survey": w[:, 5]}
 
 
 class Server:
@@ -421,19 +425,25 @@ class Server:
     def poll(self, ticket):
         r = Result()
         lat = C.c_double()
-        rc = _lib.agis_server_poll(self.h, ticket, C.byref(r), C.byref(lat))
+        ep = (C.c_uint64 * 2)()
+        rc = _lib.agis_server_poll(self.h, ticket, C.byref(r), C.byref(lat), ep)
         if rc == ERR_BUSY:
             return None
         _check(rc, "agis_server_poll")
         d = r.as_dict()
         d["latency_s"] = lat.value
+        d["admit_epoch"], d["finish_epoch"] = ep[0], ep[1]
         return d
 
     def stats(self):
         c, e = C.c_uint64(), C.c_uint64()
         p = C.c_int32()
-        _check(_lib.agis_server_stats(self.h, C.byref(c), C.byref(e), C.byref(p)), "agis_server_stats")
-        return {"completed": c.value, "epochs": e.value, "peak_slots": p.value}
+        busy, span = C.c_double(), C.c_double()
+        _check(_lib.agis_server_stats(self.h, C.byref(c), C.byref(e), C.byref(p), C.byref(busy), C.byref(span)),
+               "agis_server_stats")
+        return {"completed": c.value, "epochs": e.value, "peak_slots": p.value, "gpu_busy_s": busy.value,
+                "busy_span_s": span.value,
+                "gpu_idle_frac": (1.0 - busy.value / span.value) if span.value > 0 else None}
 
     def close(self):
         if getattr(self, "h", None):

@@ -35,7 +35,9 @@ constexpr uint64_t kStreamCC = 2;    // ... of a clustering-coefficient probe
 // One step of a compiled query as the sampler kernel reads it.
 struct DevStep {
     int32_t nb;                 // |B[i]|: number of backward neighbours
-    int16_t approx;             // D(i): 1 = f_approx, 0 = f_uniform
+    int8_t approx;              // 1: draw with the f_approx weight table (D(i) chose f_approx and
+                                // the weights are not all equal on S_tau); 0: by position / degree
+    int8_t dapprox;             // D(i) itself (1 = f_approx); only the survey's sector count reads it
     int8_t inc;                 // backward set = previous step's plus the previous vertex
     int8_t rp_mode;             // pref for |B| = 1: 0 none, 1 per-row prefix of every row,
                                 // 2 prefix of high-degree rows only (located by rp_base)
@@ -55,9 +57,12 @@ struct DevQuery {
     DevStep step[kMaxK];
 };
 
+// Words of one tile's output (AGIS_TILE_WORDS): hits, model sectors, bits of sum X,
+// bits of sum X^2, streamed part of the model sectors, survey-count sectors.
+constexpr int kTileWords = AGIS_TILE_WORDS;
+
 // A work item: `count` trials (at most kMaxSpan tiles) of query `query` starting at
-// trial `first`; the sums of its t-th tile go to out[4*(slot+t) .. 4*(slot+t)+3]
-// (hits, sectors, bits of sum X, bits of sum X^2).
+// trial `first`; the sums of its t-th tile go to out[kTileWords*(slot+t) ...].
 struct WorkItem {
     uint32_t query;
     uint32_t count;
@@ -70,7 +75,7 @@ struct DumpView {
     int32_t *emb;
     uint8_t *hit;
     double *x;
-    uint64_t *sectors;
+    uint64_t *sectors;          // 3 words per trial: model total, its streamed part, survey count
     uint64_t first;
 };
 
@@ -105,10 +110,11 @@ struct LaunchBuffers {
     size_t cap_queries = 0;
     WorkItem *d_items = nullptr;
     size_t cap_items = 0;
-    uint64_t *d_out = nullptr;  // 4 words per item slot
+    uint64_t *d_out = nullptr;  // kTileWords words per tile slot
     size_t cap_out = 0;
     uint32_t *d_counter = nullptr; // [0] work counter, [1] number of items
     void *d_scratch = nullptr;     // per-warp candidate lists of the sampler
+    bool scratch_borrowed = false; // d_scratch belongs to another LaunchBuffers (not freed here)
     size_t scratch_bytes = 0;
     uint32_t scratch_cap = 0;      // entries per list
     int scratch_grid = 0;          // CTAs the scratch was sized for
@@ -235,10 +241,13 @@ struct QueryRun {
     uint64_t max_tiles = 0;       // ceil(max_trials / 1024)
     uint64_t tiles_per_chunk = 0;
     uint64_t done_tiles = 0;      // tiles whose sums are in
+    uint64_t issued_tiles = 0;    // tiles staged for launches so far (>= done_tiles; more
+                                  // while a server's epochs are in flight)
     uint64_t trials_done = 0;
-    uint64_t hits = 0, sectors = 0;
+    uint64_t hits = 0, sectors = 0, streamed = 0, survey = 0;
     double sx = 0.0, sx2 = 0.0;
     uint64_t ck_trials = 0, ck_hits = 0, ck_sectors = 0;   // at the last checkpoint
+    uint64_t ck_streamed = 0, ck_survey = 0;
     double ck_sx = 0.0, ck_sx2 = 0.0;
     bool finished = false;
     bool converged = false;
@@ -249,10 +258,19 @@ struct QueryRun {
 int check_opts(const agis_opts *o);
 int init_run(agis_graph *g, const agis_pattern *p, const agis_opts *o, QueryRun &r);
 uint64_t next_tiles(const QueryRun &r);
+// tiles to issue next while issued_tiles - done_tiles are still in flight
+uint64_t ahead_tiles(const QueryRun &r);
 void absorb(QueryRun &r, const uint64_t *tiles, uint64_t n);
 void fill_result(const QueryRun &r, agis_result *out);
 int run_epoch_graph(agis_graph *g, std::vector<QueryRun *> &runs, const std::vector<uint64_t> &ntiles,
                     size_t total);
+// Stages an epoch into lb (its own pinned and device buffers, the scratch of
+// scratch_lb) and enqueues its captured graph on the context's stream, recording
+// `done` after the tile sums' copy to lb.h_out; no host synchronisation.
+int enqueue_epoch_graph(agis_graph *g, LaunchBuffers &lb, const LaunchBuffers &scratch_lb,
+                        std::vector<QueryRun *> &runs, const std::vector<uint64_t> &ntiles, size_t total,
+                        cudaEvent_t start, cudaEvent_t done);
+void free_buffers(LaunchBuffers &lb);
 double now_s();
 
 inline int cuda_status(cudaError_t e) { return e == cudaSuccess ? AGIS_OK : AGIS_ERR_CUDA; }

@@ -50,6 +50,8 @@ int grow_pinned(T **p, size_t *cap, size_t need, uint64_t *generation)
     return AGIS_OK;
 }
 
+}  // namespace
+
 void free_buffers(LaunchBuffers &lb)
 {
     if (lb.exec) cudaGraphExecDestroy(lb.exec);
@@ -58,13 +60,15 @@ void free_buffers(LaunchBuffers &lb)
     cudaFree(lb.d_items);
     cudaFree(lb.d_out);
     cudaFree(lb.d_counter);
-    cudaFree(lb.d_scratch);
+    if (!lb.scratch_borrowed) cudaFree(lb.d_scratch);
     cudaFreeHost(lb.h_queries);
     cudaFreeHost(lb.h_items);
     cudaFreeHost(lb.h_out);
     cudaFreeHost(lb.h_counter);
     lb = LaunchBuffers();
 }
+
+namespace {
 
 // Alg. 1: mu, population sigma^2 (clamped at 0) and eps_hat from N trials.
 void alg1(double n, double sx, double sx2, double z, double *mu, double *var, double *eps_hat)
@@ -98,7 +102,7 @@ int ensure_buffers(LaunchBuffers &lb, size_t n_queries, size_t n_items)
     int rc;
     if ((rc = grow_device(&lb.d_queries, &lb.cap_queries, n_queries, &lb.generation))) return rc;
     if ((rc = grow_device(&lb.d_items, &lb.cap_items, n_items, &lb.generation))) return rc;
-    if ((rc = grow_device(&lb.d_out, &lb.cap_out, 4 * n_items, &lb.generation))) return rc;
+    if ((rc = grow_device(&lb.d_out, &lb.cap_out, kTileWords * n_items, &lb.generation))) return rc;
     if (!lb.d_counter) {
         AGIS_CUDA_TRY(cudaMalloc(&lb.d_counter, 2 * sizeof(uint32_t)));
         AGIS_CUDA_TRY(cudaMallocHost(&lb.h_counter, 2 * sizeof(uint32_t)));
@@ -106,7 +110,7 @@ int ensure_buffers(LaunchBuffers &lb, size_t n_queries, size_t n_items)
     }
     if ((rc = grow_pinned(&lb.h_queries, &lb.hcap_queries, n_queries, &lb.generation))) return rc;
     if ((rc = grow_pinned(&lb.h_items, &lb.hcap_items, n_items, &lb.generation))) return rc;
-    if ((rc = grow_pinned(&lb.h_out, &lb.hcap_out, 4 * n_items, &lb.generation))) return rc;
+    if ((rc = grow_pinned(&lb.h_out, &lb.hcap_out, kTileWords * n_items, &lb.generation))) return rc;
     return AGIS_OK;
 }
 
@@ -210,6 +214,7 @@ int make_dev_query(agis_graph *g, const agis_pattern *p, const agis_opts *o, Dev
         DevStep &s = dq->step[i];
         s.nb = p->nback[i];
         s.approx = step_uses_table(p, i, o, g->oriented, use);
+        s.dapprox = use[i] ? 1 : 0;
         for (int j = 0; j < p->nback[i] && j < kMaxK; ++j) s.back[j] = (int8_t)p->back[i][j];
         if (i >= 2) {
             // back(i) == back(i-1) + {i-1}?
@@ -268,31 +273,40 @@ int init_run(agis_graph *g, const agis_pattern *p, const agis_opts *o, QueryRun 
     return make_dev_query(g, p, o, &r.dq, &r.t_prep);
 }
 
-// Tiles to run next for one query: the first epoch covers min_trials (whole
-// chunks); later ones aim at the trial count Alg. 1's own formula predicts,
-// N ~ (z sigma / (eps mu))^2, between one chunk and four times the work so far.
-uint64_t next_tiles(const QueryRun &r)
+// Tiles to run after the first `from` tiles of one query: the first epoch covers
+// min_trials (whole chunks); later ones aim at the trial count Alg. 1's own formula
+// predicts from the sums absorbed so far, N ~ (z sigma / (eps mu))^2, between one
+// chunk and four times the work so far.  Tiles already issued but not absorbed
+// count as work done.
+static uint64_t tiles_after(const QueryRun &r, uint64_t from)
 {
-    const uint64_t left = r.max_tiles - r.done_tiles;
+    const uint64_t left = r.max_tiles > from ? r.max_tiles - from : 0;
     if (r.o.eps <= 0.0) return left;
     const uint64_t tpc = r.tiles_per_chunk;
     uint64_t want;
-    if (r.done_tiles == 0) {
+    if (from == 0) {
         const uint64_t min_tiles = (r.o.min_trials + kTile - 1) / kTile;
         want = std::max<uint64_t>(tpc, (min_tiles + tpc - 1) / tpc * tpc);
+    } else if (r.trials_done == 0) {
+        want = tpc;               // nothing absorbed yet: one more chunk
     } else {
         const double n = (double)r.trials_done;
+        const double issued = (double)(from * kTile);
         const double mu = r.sx / n;
         double var = r.sx2 / n - mu * mu;
         if (var < 0) var = 0;
-        double need = mu > 0 ? (r.z * r.z * var) / (r.o.eps * r.o.eps * mu * mu) : 4.0 * n;
-        need = std::min(need, 4.0 * n + 1.0);
-        const double more = std::max(need - n, (double)r.o.chunk_trials);
+        double need = mu > 0 ? (r.z * r.z * var) / (r.o.eps * r.o.eps * mu * mu) : 4.0 * issued;
+        need = std::min(need, 4.0 * issued + 1.0);
+        const double more = std::max(need - issued, (double)r.o.chunk_trials);
         want = (uint64_t)std::ceil(more / kTile);
         want = (want + tpc - 1) / tpc * tpc;
     }
     return std::min(want, left);
 }
+
+uint64_t next_tiles(const QueryRun &r) { return tiles_after(r, r.done_tiles); }
+
+uint64_t ahead_tiles(const QueryRun &r) { return r.finished ? 0 : tiles_after(r, r.issued_tiles); }
 
 // Folds the tile sums of tiles [done_tiles, done_tiles + n) (in index order) into
 // the run, evaluating Alg. 1 at each chunk checkpoint.  Stops at the first
@@ -300,7 +314,7 @@ uint64_t next_tiles(const QueryRun &r)
 void absorb(QueryRun &r, const uint64_t *tiles, uint64_t n)
 {
     for (uint64_t j = 0; j < n && !r.finished; ++j) {
-        const uint64_t *o = tiles + 4 * j;
+        const uint64_t *o = tiles + kTileWords * j;
         const uint64_t tile_idx = r.done_tiles;
         const uint64_t first = tile_idx * kTile;
         const uint64_t cnt = std::min<uint64_t>(kTile, r.o.max_trials > first ? r.o.max_trials - first : 0);
@@ -309,6 +323,8 @@ void absorb(QueryRun &r, const uint64_t *tiles, uint64_t n)
         std::memcpy(&s2, &o[3], 8);
         r.hits += o[0];
         r.sectors += o[1];
+        r.streamed += o[4];
+        r.survey += o[5];
         r.sx += s;
         r.sx2 += s2;
         r.trials_done += cnt;
@@ -318,6 +334,8 @@ void absorb(QueryRun &r, const uint64_t *tiles, uint64_t n)
         r.ck_trials = r.trials_done;
         r.ck_hits = r.hits;
         r.ck_sectors = r.sectors;
+        r.ck_streamed = r.streamed;
+        r.ck_survey = r.survey;
         r.ck_sx = r.sx;
         r.ck_sx2 = r.sx2;
         if (r.o.eps > 0.0 && r.trials_done >= r.o.min_trials) {
@@ -351,6 +369,8 @@ void fill_result(const QueryRun &r, agis_result *out)
     out->trials = r.ck_trials;
     out->hits = r.ck_hits;
     out->sectors = r.ck_sectors;
+    out->sectors_streamed = r.ck_streamed;
+    out->sectors_survey = r.ck_survey;
     out->converged = r.converged ? 1 : 0;
     out->launches = r.launches;
     out->t_prep_s = r.t_prep;
@@ -373,11 +393,11 @@ size_t stage_items(LaunchBuffers &lb, std::vector<QueryRun *> &runs, const std::
 {
     size_t k = 0, m = 0;
     for (size_t q = 0; q < runs.size(); ++q) {
-        const QueryRun &r = *runs[q];
+        QueryRun &r = *runs[q];
         lb.h_queries[q] = r.dq;
         for (uint64_t j = 0; j < ntiles[q]; j += (uint64_t)span) {
             const uint64_t nt = std::min<uint64_t>((uint64_t)span, ntiles[q] - j);
-            const uint64_t first = (r.done_tiles + j) * kTile;
+            const uint64_t first = (r.issued_tiles + j) * kTile;
             WorkItem &w = lb.h_items[m++];
             w.query = (uint32_t)q;
             w.count = (uint32_t)std::min<uint64_t>(nt * kTile, r.o.max_trials - first);
@@ -385,6 +405,7 @@ size_t stage_items(LaunchBuffers &lb, std::vector<QueryRun *> &runs, const std::
             w.slot = k;
             k += nt;
         }
+        r.issued_tiles += ntiles[q];
     }
     return m;
 }
@@ -414,26 +435,33 @@ int run_epoch_direct(agis_graph *g, std::vector<QueryRun *> &runs, const std::ve
     if ((rc = ensure_scratch(g, lb, grid)) != AGIS_OK) return rc;
     rc = launch_sampler(g, lb, grid, nullptr, st, 0, 0, nullptr, any_anchor(runs));
     if (rc != AGIS_OK) return rc;
-    AGIS_CUDA_TRY(cudaMemcpyAsync(lb.h_out, lb.d_out, sizeof(uint64_t) * 4 * total, cudaMemcpyDeviceToHost, st));
+    AGIS_CUDA_TRY(cudaMemcpyAsync(lb.h_out, lb.d_out, sizeof(uint64_t) * kTileWords * total, cudaMemcpyDeviceToHost, st));
     AGIS_CUDA_TRY(cudaStreamSynchronize(st));
     return AGIS_OK;
 }
 
 // The batched epoch as a CUDA graph: H2D of queries, items and counters, the
 // persistent sampler, D2H of the tile sums.  Built once per buffer generation and
-// grid; sizes are patched per epoch.
-int run_epoch_graph(agis_graph *g, std::vector<QueryRun *> &runs, const std::vector<uint64_t> &ntiles,
-                    size_t total)
+// grid; sizes are patched per epoch.  `start` and `done` (either may be null) are
+// recorded around the graph launch.
+int enqueue_epoch_graph(agis_graph *g, LaunchBuffers &lb, const LaunchBuffers &scratch_lb,
+                        std::vector<QueryRun *> &runs, const std::vector<uint64_t> &ntiles, size_t total,
+                        cudaEvent_t start, cudaEvent_t done)
 {
-    LaunchBuffers &lb = g->lb;
     cudaStream_t st = g->ctx->stream;
     int rc = ensure_buffers(lb, runs.size(), total);
     if (rc != AGIS_OK) return rc;
-    const int grid = grid_for(g, (size_t)g->ctx->sm_count * 64);
+    const int grid = std::min(grid_for(g, (size_t)g->ctx->sm_count * 64), scratch_lb.scratch_grid);
+    if (&lb != &scratch_lb && (lb.d_scratch != scratch_lb.d_scratch || lb.scratch_cap != scratch_lb.scratch_cap)) {
+        lb.d_scratch = scratch_lb.d_scratch;
+        lb.scratch_cap = scratch_lb.scratch_cap;
+        lb.scratch_grid = scratch_lb.scratch_grid;
+        lb.scratch_borrowed = true;
+        ++lb.generation;
+    }
     const size_t n = stage_items(lb, runs, ntiles, span_for(g, total, grid));
     lb.h_counter[0] = 0;
     lb.h_counter[1] = (uint32_t)n;
-    if ((rc = ensure_scratch(g, lb, grid)) != AGIS_OK) return rc;
     const bool anchor = any_anchor(runs);
     if (!lb.exec || lb.graph_generation != lb.generation || lb.graph_grid != grid || lb.graph_anchor != anchor) {
         if (lb.exec) cudaGraphExecDestroy(lb.exec);
@@ -450,7 +478,7 @@ int run_epoch_graph(agis_graph *g, std::vector<QueryRun *> &runs, const std::vec
         rc = add_sampler_node(g, lb, grid, lb.graph, &lb.n_h2d_c, 1, &lb.n_kernel, anchor);
         if (rc != AGIS_OK) return rc;
         AGIS_CUDA_TRY(cudaGraphAddMemcpyNode1D(&lb.n_d2h, lb.graph, &lb.n_kernel, 1, lb.h_out, lb.d_out,
-                                               4 * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+                                               kTileWords * sizeof(uint64_t), cudaMemcpyDeviceToHost));
         AGIS_CUDA_TRY(cudaGraphInstantiate(&lb.exec, lb.graph, 0));
         lb.graph_generation = lb.generation;
         lb.graph_anchor = anchor;
@@ -461,11 +489,25 @@ int run_epoch_graph(agis_graph *g, std::vector<QueryRun *> &runs, const std::vec
     AGIS_CUDA_TRY(cudaGraphExecMemcpyNodeSetParams1D(lb.exec, lb.n_h2d_i, lb.d_items, lb.h_items,
                                                      sizeof(WorkItem) * std::max<size_t>(n, 1), cudaMemcpyHostToDevice));
     AGIS_CUDA_TRY(cudaGraphExecMemcpyNodeSetParams1D(lb.exec, lb.n_d2h, lb.h_out, lb.d_out,
-                                                     sizeof(uint64_t) * 4 * std::max<size_t>(total, 1),
+                                                     sizeof(uint64_t) * kTileWords * std::max<size_t>(total, 1),
                                                      cudaMemcpyDeviceToHost));
+    if (start) AGIS_CUDA_TRY(cudaEventRecord(start, st));
     count_launch();
     AGIS_CUDA_TRY(cudaGraphLaunch(lb.exec, st));
-    AGIS_CUDA_TRY(cudaStreamSynchronize(st));
+    if (done) AGIS_CUDA_TRY(cudaEventRecord(done, st));
+    return AGIS_OK;
+}
+
+int run_epoch_graph(agis_graph *g, std::vector<QueryRun *> &runs, const std::vector<uint64_t> &ntiles,
+                    size_t total)
+{
+    LaunchBuffers &lb = g->lb;
+    const int grid = grid_for(g, (size_t)g->ctx->sm_count * 64);
+    int rc = ensure_scratch(g, lb, grid);
+    if (rc != AGIS_OK) return rc;
+    rc = enqueue_epoch_graph(g, lb, lb, runs, ntiles, total, nullptr, nullptr);
+    if (rc != AGIS_OK) return rc;
+    AGIS_CUDA_TRY(cudaStreamSynchronize(g->ctx->stream));
     return AGIS_OK;
 }
 
@@ -504,7 +546,7 @@ int drive(agis_graph *g, std::vector<QueryRun *> &runs, bool use_graph, size_t m
         size_t k = 0;
         for (size_t q = 0; q < active.size(); ++q) {
             active[q]->launches++;
-            absorb(*active[q], g->lb.h_out + 4 * k, ntiles[q]);
+            absorb(*active[q], g->lb.h_out + kTileWords * k, ntiles[q]);
             k += ntiles[q];
         }
     }
@@ -713,7 +755,7 @@ extern "C" int agis_dump_trials(agis_graph *g, const agis_pattern *p, const agis
     if ((emb && cudaMalloc(&dv.emb, sizeof(int32_t) * kMaxK * c) != cudaSuccess) ||
         (hit && cudaMalloc(&dv.hit, c) != cudaSuccess) ||
         (x && cudaMalloc(&dv.x, sizeof(double) * c) != cudaSuccess) ||
-        (sectors && cudaMalloc(&dv.sectors, sizeof(uint64_t) * c) != cudaSuccess)) {
+        (sectors && cudaMalloc(&dv.sectors, 3 * sizeof(uint64_t) * c) != cudaSuccess)) {
         cleanup();
         return AGIS_ERR_NOMEM;
     }
@@ -730,7 +772,7 @@ extern "C" int agis_dump_trials(agis_graph *g, const agis_pattern *p, const agis
     if (rc == AGIS_OK && emb && cudaMemcpy(emb, dv.emb, sizeof(int32_t) * kMaxK * c, cudaMemcpyDeviceToHost) != cudaSuccess) rc = AGIS_ERR_CUDA;
     if (rc == AGIS_OK && hit && cudaMemcpy(hit, dv.hit, c, cudaMemcpyDeviceToHost) != cudaSuccess) rc = AGIS_ERR_CUDA;
     if (rc == AGIS_OK && x && cudaMemcpy(x, dv.x, sizeof(double) * c, cudaMemcpyDeviceToHost) != cudaSuccess) rc = AGIS_ERR_CUDA;
-    if (rc == AGIS_OK && sectors && cudaMemcpy(sectors, dv.sectors, sizeof(uint64_t) * c, cudaMemcpyDeviceToHost) != cudaSuccess) rc = AGIS_ERR_CUDA;
+    if (rc == AGIS_OK && sectors && cudaMemcpy(sectors, dv.sectors, 3 * sizeof(uint64_t) * c, cudaMemcpyDeviceToHost) != cudaSuccess) rc = AGIS_ERR_CUDA;
     cleanup();
     return rc;
 }

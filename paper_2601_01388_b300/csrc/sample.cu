@@ -58,12 +58,19 @@ __device__ __forceinline__ uint64_t sec_search(int64_t L, int w)
 }
 
 // Sectors to test d_a entries for membership in a row of m entries: the cheaper of
-// reading the row once (a merge) and one search per entry.
-__device__ __forceinline__ uint64_t row_check_sectors(int64_t da, int64_t m)
+// reading the row once (a merge, streamed) and one search per entry; `survey` gets
+// the search count alone.
+__device__ __forceinline__ uint64_t row_check_sectors(int64_t da, int64_t m, uint64_t &streamed,
+                                                      uint64_t &survey)
 {
     const uint64_t merge = (uint64_t)((4 * (m > 0 ? m : 1) + 31) / 32);
     const uint64_t search = (uint64_t)da * sec_search(m, 4);
-    return merge < search ? merge : search;
+    survey += search;
+    if (merge < search) {
+        streamed += merge;
+        return merge;
+    }
+    return search;
 }
 
 // Neighbour bitmap of vertex u, or null when u has none.
@@ -213,9 +220,11 @@ __device__ __forceinline__ uint64_t warp_incl_scan(uint64_t v, int lane)
     return v;
 }
 
+// Per-trial output: X, hit flag and the three sector counts (the model, its streamed
+// part, and the survey's plain count).
 struct TrialOut {
     double x;
-    uint64_t sectors;
+    uint64_t sectors, streamed, survey;
     int hit;
 };
 
@@ -551,13 +560,20 @@ __device__ __forceinline__ uint64_t closing_sectors(const GraphView &g, const De
     return s;
 }
 
+// The streamed and survey counts are warp-uniform and kept in the warp's shared
+// words wsec[0..1] (lane 0 adds to them) to spare registers; sec stays in registers.
+#define STORE_SECTORS(o) do { (o).sectors = sec; (o).streamed = wsec[0]; (o).survey = wsec[1]; } while (0)
+#define ADD_ST(v) do { if (lane == 0) wsec[0] += (v); } while (0)
+#define ADD_SV(v) do { if (lane == 0) wsec[1] += (v); } while (0)
+
 template <bool kAnchor>
 __device__ TrialOut run_trial(const GraphView &g, const DevQuery &Q, uint64_t t, int32_t *tau_s,
-                              const WarpSets &ws, const uint64_t *top, int lane)
+                              const WarpSets &ws, const uint64_t *top, uint64_t *wsec, int lane)
 {
-    TrialOut out{0.0, 0, 0};
+    TrialOut out{0.0, 0, 0, 0, 0};
     double X = 1.0;
-    uint64_t sec = 0;
+    uint64_t sec = 0;      // model sectors (streamed part and survey count in wsec)
+    if (lane == 0) wsec[0] = wsec[1] = 0;
     int cur = -1;          // scratch list holding S of the previous step (-1: none)
     uint32_t n_cur = 0;
     if (lane < kMaxK) tau_s[lane] = -1;
@@ -604,7 +620,8 @@ __device__ TrialOut run_trial(const GraphView &g, const DevQuery &Q, uint64_t t,
             // ---- step 1: the whole vertex set
             W = Q.W1;
             sec += sec_search(g.nv + 1, 8) + (S.approx ? 1 : 0);
-            if (W == 0) { out.sectors = sec; return out; }
+            ADD_SV(sec_search(g.nv + 1, 8) + (S.approx ? 1 : 0));
+            if (W == 0) { STORE_SECTORS(out); return out; }
             const uint64_t r = draw_below(W, t, 1, kStreamTrial, Q.seed);
             const uint64_t *P = S.approx ? S.pref : (const uint64_t *)(g.off + 1);
             v = (int32_t)warp_find_top(P, g.nv, r, top, lane);
@@ -616,8 +633,12 @@ __device__ TrialOut run_trial(const GraphView &g, const DevQuery &Q, uint64_t t,
             const int32_t a = tau_s[jb];
             const int64_t a_start = __ldg(g.off + a);
             const int64_t d = __ldg(g.off + a + 1) - a_start;
-            sec += 1 + (uint64_t)(i - 1) * sec_search(d, 4) + (S.approx ? sec_search(d, 8) + 1 : 0) + 1;
-            if (anch) sec += closing_sectors(g, S, tau_s, jb);
+            {
+                const uint64_t base = 1 + (uint64_t)(i - 1) * sec_search(d, 4) + 1 +
+                                      (anch ? closing_sectors(g, S, tau_s, jb) : 0);
+                sec += base + (S.approx ? sec_search(d, 8) + 1 : 0);
+                ADD_SV(base + (S.dapprox ? sec_search(d, 8) + 1 : 0));
+            }
             // trajectory members inside a's row (lane j checks tau_j): excluded by
             // vertex id, so a hub row needs one bitmap probe and no search
             bool member = false;
@@ -637,13 +658,13 @@ __device__ TrialOut run_trial(const GraphView &g, const DevQuery &Q, uint64_t t,
             const uint64_t *P = S.approx ? Prow : nullptr;
             const uint64_t total = d <= 0 ? 0 : (S.approx ? __ldg(P + d - 1) : (uint64_t)d);
             W = total - excl;
-            if (W == 0) { out.sectors = sec; return out; }
+            if (W == 0) { STORE_SECTORS(out); return out; }
             const uint64_t r = draw_below(W, t, (uint64_t)(i + 1), kStreamTrial, Q.seed);
             const int64_t pos = warp_find(P, d, r, xmask, xkey, xq, g.cols + a_start, lane);
             v = __ldg(g.cols + a_start + pos);
             qv = S.approx ? __ldg(S.q + v) : 1u;
             cur = -1;
-            if (anch && !closes_all(g, S, tau_s, jb, v, lane)) { out.sectors = sec; return out; }
+            if (anch && !closes_all(g, S, tau_s, jb, v, lane)) { STORE_SECTORS(out); return out; }
             STEP_T1(1)
         } else {
             // ---- several backward neighbours (or one, with no row-prefix table):
@@ -658,14 +679,14 @@ __device__ TrialOut run_trial(const GraphView &g, const DevQuery &Q, uint64_t t,
                 if (da < 0 || len < da) { da = len; ai = b; a_start = s0; }
             }
             int n_other = 0;
-            uint64_t search_sec = 0;
+            uint64_t search_sec = 0, merge_st = 0, search_sv = 0;
             for (int b = 0; b < S.nb; ++b) {
                 if (b == ai) continue;
                 const int32_t u = tau_s[S.back[b]];
                 o_start[n_other] = __ldg(g.off + u);
                 o_len[n_other] = __ldg(g.off + u + 1) - o_start[n_other];
                 o_bits[n_other] = bits_of(g, u);
-                search_sec += row_check_sectors(da, o_len[n_other]);
+                search_sec += row_check_sectors(da, o_len[n_other], merge_st, search_sv);
                 ++n_other;
             }
             // an anchor draw filters only trajectory members here; the other rows are
@@ -673,10 +694,15 @@ __device__ TrialOut run_trial(const GraphView &g, const DevQuery &Q, uint64_t t,
             const int n_filter = anch ? 0 : n_other;
             if (S.nb == 1 || anch) {
                 // the cost model counts the method's single-backward draw, whichever way it runs
-                sec += 1 + (uint64_t)(i - 1) * sec_search(da, 4) + (S.approx ? sec_search(da, 8) + 1 : 0) + 1;
-                if (anch) sec += closing_sectors(g, S, tau_s, jb);
+                const uint64_t base = 1 + (uint64_t)(i - 1) * sec_search(da, 4) + 1 +
+                                      (anch ? closing_sectors(g, S, tau_s, jb) : 0);
+                sec += base + (S.approx ? sec_search(da, 8) + 1 : 0);
+                ADD_SV(base + (S.dapprox ? sec_search(da, 8) + 1 : 0));
             } else {
-                sec += (uint64_t)S.nb + (uint64_t)((4 * da + 31) / 32) + search_sec;
+                const uint64_t scan = (uint64_t)((4 * da + 31) / 32);
+                sec += (uint64_t)S.nb + scan + search_sec;
+                ADD_ST(scan + merge_st);
+                ADD_SV((uint64_t)S.nb + scan + search_sv);
             }
             // S of the previous step is reusable when this step's backward set is the
             // previous one plus the previous vertex: S_i = S_{i-1} & N(v_{i-1})
@@ -731,10 +757,11 @@ __device__ TrialOut run_trial(const GraphView &g, const DevQuery &Q, uint64_t t,
             }
             if (listed) {
                 if (S.approx && S.nb > 1 && !anch) sec += n;
+                if (S.dapprox && S.nb > 1 && !anch) ADD_SV(n);
                 W = Wl;
                 cur = nxt;
                 n_cur = n;
-                if (W == 0) { out.sectors = sec; return out; }
+                if (W == 0) { STORE_SECTORS(out); return out; }
                 const uint64_t r = draw_below(W, t, (uint64_t)(i + 1), kStreamTrial, Q.seed);
                 // equal weights: the r-th survivor (r < W = n)
                 const int64_t j = S.approx ? warp_find(ws.pw[cur], n, r, 0u, 0, 0, nullptr, lane) : (int64_t)r;
@@ -742,7 +769,7 @@ __device__ TrialOut run_trial(const GraphView &g, const DevQuery &Q, uint64_t t,
                 qv = S.approx ? ws.pw[cur][j] - (j > 0 ? ws.pw[cur][j - 1] : 0) : 1u;
                 if (anch) {
                     cur = -1;
-                    if (!closes_all(g, S, tau_s, jb, v, lane)) { out.sectors = sec; return out; }
+                    if (!closes_all(g, S, tau_s, jb, v, lane)) { STORE_SECTORS(out); return out; }
                 }
                 X = X * ((double)W / (double)qv);
                 STEP_T1(reuse ? 3 : 2)
@@ -785,8 +812,9 @@ __device__ TrialOut run_trial(const GraphView &g, const DevQuery &Q, uint64_t t,
                 }
             }
             if (S.approx && S.nb > 1 && !anch) sec += nsurv;
+            if (S.dapprox && S.nb > 1 && !anch) ADD_SV(nsurv);
             W = running;
-            if (W == 0) { out.sectors = sec; return out; }
+            if (W == 0) { STORE_SECTORS(out); return out; }
             const uint64_t r = draw_below(W, t, (uint64_t)(i + 1), kStreamTrial, Q.seed);
             if (r >= last_before) {
                 const bool hit = last_w > 0 && last_before + last_incl > r;
@@ -819,7 +847,7 @@ __device__ TrialOut run_trial(const GraphView &g, const DevQuery &Q, uint64_t t,
         }
         if (i > 0 && !direct) {
             STEP_T1(4)
-            if (anch && !closes_all(g, S, tau_s, jb, v, lane)) { out.sectors = sec; return out; }
+            if (anch && !closes_all(g, S, tau_s, jb, v, lane)) { STORE_SECTORS(out); return out; }
         }
         X = X * ((double)W / (double)qv);
         __syncwarp();
@@ -828,9 +856,12 @@ __device__ TrialOut run_trial(const GraphView &g, const DevQuery &Q, uint64_t t,
     }
     out.x = X;
     out.hit = 1;
-    out.sectors = sec;
+    STORE_SECTORS(out);
     return out;
 }
+#undef STORE_SECTORS
+#undef ADD_ST
+#undef ADD_SV
 
 // Work items come from `items`, or, when it is null, are implicit: item j covers
 // trials [implicit_first + kTile j, ...) of query 0 up to implicit_count trials and
@@ -851,9 +882,10 @@ __global__ void __launch_bounds__(kBlock, AGIS_MIN_BLOCKS) sample_kernel(GraphVi
     __shared__ double red[kBlock];
     __shared__ double red2[kBlock];
     __shared__ int32_t tau_s[kWarps][kMaxK];
+    __shared__ uint64_t s_wsec[kWarps][2];
     __shared__ uint64_t s_top[kTopSplitters];
     __shared__ uint32_t s_item, s_next, s_hits[kMaxSpan];
-    __shared__ unsigned long long s_sec[kMaxSpan];
+    __shared__ unsigned long long s_sec[kMaxSpan][3];
     __shared__ int s_query, s_reload;
     __shared__ WorkItem s_it;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -893,7 +925,7 @@ __global__ void __launch_bounds__(kBlock, AGIS_MIN_BLOCKS) sample_kernel(GraphVi
             s_next = 0;
             for (int t = 0; t < kMaxSpan; ++t) {
                 s_hits[t] = 0;
-                s_sec[t] = 0;
+                s_sec[t][0] = s_sec[t][1] = s_sec[t][2] = 0;
             }
         }
         __syncthreads();
@@ -921,16 +953,22 @@ __global__ void __launch_bounds__(kBlock, AGIS_MIN_BLOCKS) sample_kernel(GraphVi
             tt = __shfl_sync(kFull, tt, 0);
             if (tt >= it.count) break;
             const uint64_t t = it.first + tt;
-            const TrialOut r = run_trial<kAnchor>(g, sq, t, tau_s[warp], ws, s_top, lane);
+            const TrialOut r = run_trial<kAnchor>(g, sq, t, tau_s[warp], ws, s_top, s_wsec[warp], lane);
             if (lane == 0) {
                 xs[tt] = r.x;
                 if (r.hit) atomicAdd(&s_hits[tt / kTile], 1u);
-                atomicAdd(&s_sec[tt / kTile], (unsigned long long)r.sectors);
+                atomicAdd(&s_sec[tt / kTile][0], (unsigned long long)r.sectors);
+                atomicAdd(&s_sec[tt / kTile][1], (unsigned long long)r.streamed);
+                atomicAdd(&s_sec[tt / kTile][2], (unsigned long long)r.survey);
                 if (kDump) {
                     const uint64_t d = t - dump.first;
                     if (dump.hit) dump.hit[d] = (uint8_t)r.hit;
                     if (dump.x) dump.x[d] = r.x;
-                    if (dump.sectors) dump.sectors[d] = r.sectors;
+                    if (dump.sectors) {
+                        dump.sectors[3 * d] = r.sectors;
+                        dump.sectors[3 * d + 1] = r.streamed;
+                        dump.sectors[3 * d + 2] = r.survey;
+                    }
                 }
             }
             if (kDump && dump.emb && lane < kMaxK) dump.emb[(t - dump.first) * kMaxK + lane] = tau_s[warp][lane];
@@ -958,11 +996,13 @@ __global__ void __launch_bounds__(kBlock, AGIS_MIN_BLOCKS) sample_kernel(GraphVi
                 __syncthreads();
             }
             if (threadIdx.x == 0) {
-                uint64_t *o = tile_out + 4 * ((uint64_t)it.slot + tl);
+                uint64_t *o = tile_out + kTileWords * ((uint64_t)it.slot + tl);
                 o[0] = s_hits[tl];
-                o[1] = s_sec[tl];
+                o[1] = s_sec[tl][0];
                 o[2] = (uint64_t)__double_as_longlong(red[0]);
                 o[3] = (uint64_t)__double_as_longlong(red2[0]);
+                o[4] = s_sec[tl][1];
+                o[5] = s_sec[tl][2];
             }
             __syncthreads();
         }

@@ -177,6 +177,35 @@ def chung_lu_graph(n: int, gamma: float = 2.1, mean_degree: float = 32.0, seed=1
     return csr_from_edges(n, perm[src], perm[dst])
 
 
+def dense_graph_rows(n: int, u0: int, u1: int):
+    """Rows u0..u1-1 of dense_graph(n) as a boolean adjacency block ((u1-u0) x n).
+    {u, v} (u != v) is an edge unless (u XOR v) & 7 == 0, (u + v) & 31 == 5,
+    u & v & 0x300 == 0x300 or (u | v) & 0x1C00 == 0; every rule is symmetric in u
+    and v, and u XOR u = 0 drops the diagonal.  About 80% of the pairs are edges; the
+    last two rules split the vertices into degree classes by bits 8-12 of their id."""
+    u = np.arange(u0, u1, dtype=np.int64)[:, None]
+    w = np.arange(n, dtype=np.int64)[None, :]
+    keep = (((u ^ w) & 7) != 0) & (((u + w) & 31) != 5)
+    keep &= ((u & w & 0x300) != 0x300) & (((u | w) & 0x1C00) != 0)
+    return keep
+
+
+def dense_graph(n: int, rows_per_chunk: int = 256):
+    """The dense, deterministic graph of dense_graph_rows as a sorted CSR, built in two
+    passes over row blocks (counts, then columns).  With n = 54000 it has about 2.3e9
+    directed entries, past the int32 range of CSR positions."""
+    off = np.zeros(n + 1, dtype=np.int64)
+    for u0 in range(0, n, rows_per_chunk):
+        u1 = min(n, u0 + rows_per_chunk)
+        off[u0 + 1:u1 + 1] = dense_graph_rows(n, u0, u1).sum(axis=1)
+    np.cumsum(off, out=off)
+    cols = np.empty(int(off[-1]), dtype=np.int32)
+    for u0 in range(0, n, rows_per_chunk):
+        u1 = min(n, u0 + rows_per_chunk)
+        cols[off[u0]:off[u1]] = np.nonzero(dense_graph_rows(n, u0, u1))[1].astype(np.int32)
+    return off, cols
+
+
 # --------------------------------------------------------------------------
 # Patterns (k vertices, undirected edge list)
 # --------------------------------------------------------------------------

@@ -169,7 +169,7 @@ def dump_pair(agis, oracle_mod, graph, name, first, count, **kw):
     q = oracle_mod.Query(off, cols, k, edges, nsum=nsum, hits=hits, c_min=CMIN, mode=mode,
                          beta=kw.get("beta", 0.8), seed=kw["seed"], terms=kw.get("terms", 0))
     oemb, ohit, ox, osec = q.trials(first, count)
-    bad = np.nonzero((emb != oemb).any(axis=1) | (hit != ohit) | (x != ox) | (sec != osec))[0]
+    bad = np.nonzero((emb != oemb).any(axis=1) | (hit != ohit) | (x != ox) | (sec != osec).any(axis=1))[0]
     assert len(bad) == 0, (name, kw, int(bad[0]))
     return hit
 

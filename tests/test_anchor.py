@@ -97,7 +97,7 @@ def compare(agis, oracle_mod, gr, name, mode, first, count, seed=21):
                                         first, count)
     q = oracle_mod.Query(off, cols, k, edges, nsum=nsum, hits=hits, c_min=CMIN, mode=mode, seed=seed, anchor=True)
     oemb, ohit, ox, osec = q.trials(first, count)
-    bad = np.nonzero((emb != oemb).any(axis=1) | (hit != ohit) | (x != ox) | (sec != osec))[0]
+    bad = np.nonzero((emb != oemb).any(axis=1) | (hit != ohit) | (x != ox) | (sec != osec).any(axis=1))[0]
     assert len(bad) == 0, (name, mode, int(bad[0]), emb[bad[0]], oemb[bad[0]], sec[bad[0]], osec[bad[0]])
     return hit
 

@@ -32,3 +32,44 @@ def test_reference_arm_prints_one_contract_line():
     assert cb["kind"] == "oracle" and cb["cores"] == bench.host_cores() and cb["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": "samples/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
+
+
+def test_driver_command_fits_its_time_limit():
+    """The round-end command (--gpus 1 --steps 20 --warmup 5) at the stated floor
+    rates: every leg's upper bound (capped queries run to their caps) sums to less
+    than the deadline after which optional legs are skipped, and the deadline leaves
+    room under the 1800 s limit for the CPU baseline and the JSON line."""
+    sys.path.insert(0, ROOT)
+    import bench
+    args = bench.parse_args(["--gpus", "1", "--steps", "20", "--warmup", "5"])
+    plan = bench.plan_seconds(args)
+    assert args.log2_trials == 28 and args.scale == 22 and args.batch64
+    assert plan["timed"] == 20 * 2 ** 28 / bench.RATE_FLOOR["bench"]
+    assert sum(plan.values()) <= args.deadline_s, plan
+    assert args.deadline_s + 200 < 1800
+    # the default (no flags) run finishes within minutes
+    d = bench.parse_args([])
+    assert d.steps * 2 ** d.log2_trials / bench.RATE_FLOOR["bench"] <= 180
+
+
+def test_ncu_summary_round_trip(tmp_path):
+    """--summarize-ncu turns an ncu CSV of sampler launches into the JSON summary that
+    the benchmark reads back (keyed by the sampler's source hash)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    hdr = '"ID","Process ID","Process Name","Host Name","Kernel Name","Context","Stream","Block Size",' \
+          '"Grid Size","Device","CC","Section Name","Metric Name","Metric Unit","Metric Value"\n'
+    rows = []
+    for lid, (rd, wr, ns) in enumerate([(4.0, 1.0, 2.0), (2.0, 0.5, 1.0)]):
+        for name, unit, val in (("dram__bytes_read.sum", "Gbyte", rd), ("dram__bytes_write.sum", "Gbyte", wr),
+                                ("gpu__time_duration.sum", "msecond", ns)):
+            rows.append(f'"{lid}","1","python","h","void agis::sample_kernel<0, 0>(...)","1","7","(256, 1, 1)",'
+                        f'"(592, 1, 1)","0","10.3","Command line profiler metrics","{name}","{unit}","{val}"\n')
+    csv_path = tmp_path / "dram.csv"
+    csv_path.write_text("==PROF== noise\n" + hdr + "".join(rows))
+    out = tmp_path / "summary.json"
+    s = bench.summarize_ncu(str(csv_path), str(out), ["4-clique", "5-cycle"], 1 << 20, "ncu ...", "w")
+    assert s["per_pattern"]["4-clique"]["dram_bytes_per_trial"] == 5e9 / (1 << 20)
+    assert s["per_pattern"]["5-cycle"]["dram_gbs"] == 2.5e9 / 1e6
+    got = bench.profile_traffic(str(out))
+    assert got == {"4-clique": 5e9 / (1 << 20), "5-cycle": 2.5e9 / (1 << 20)}

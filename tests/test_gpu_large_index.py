@@ -1,0 +1,155 @@
+"""Parity on the int64 path: a graph with more than 2^31 directed CSR entries.
+
+Offsets, row positions, row-prefix tables (full and partial) and candidate lists all
+index past the int32 range here, which the scale-28 configuration relies on.  The
+graph is inputs.dense_graph(54000) (about 2.3e9 entries, 9.2 GB of columns), built in
+shared memory by a spawn-started process pool that also runs the CPU oracle's
+trials.  The compared queries use weights that read neither the neighbour-degree
+sums nor the clustering coefficients -- f_uniform, and f_approx with only T[F1]
+(the first version of the Sec. 6.2 ablation), w = binom(d - |B|, |F1|) -- so the
+oracle needs no Sec. 4.4 statistics of the big graph (2.3e9 probes would take it
+tens of CPU-minutes); test_weights_without_statistics pins that premise on a small
+graph.  Trials 0..N-1 of the GPU are dumped under the default memory policy and
+under a row-prefix budget that gives only the highest-degree rows a prefix, and
+compared with the oracle's bit for bit (trajectories, hit flags, FP64 outputs,
+sector counts)."""
+import multiprocessing as mp
+import os
+from multiprocessing import shared_memory
+
+import numpy as np
+import pytest
+
+from paper_2601_01388_b300 import inputs as I
+
+N_VERTICES = 54000
+CASES = [("4-clique", 1, 1, 2048), ("4-clique", 2, 0, 2048), ("5-cycle", 1, 1, 4096), ("5-cycle", 2, 0, 4096)]
+BLOCK = 256
+
+_W = {}
+
+
+def _attach(names, nv, nnz):
+    key = tuple(names)
+    if _W.get("key") != key:
+        shm = [shared_memory.SharedMemory(name=n) for n in names]
+        _W.update(key=key, shm=shm,
+                  off=np.ndarray((nv + 1,), dtype=np.int64, buffer=shm[0].buf),
+                  cols=np.ndarray((nnz,), dtype=np.int32, buffer=shm[1].buf), queries={})
+    return _W["off"], _W["cols"]
+
+
+def _count_rows(n, u0, u1):
+    return I.dense_graph_rows(n, u0, u1).sum(axis=1)
+
+
+def _fill_rows(names, n, nnz, u0, u1):
+    off, cols = _attach(names, n, nnz)
+    cols[off[u0]:off[u1]] = np.nonzero(I.dense_graph_rows(n, u0, u1))[1].astype(np.int32)
+    return u1 - u0
+
+
+def _oracle_trials(names, n, nnz, name, mode, terms, seed, first, count):
+    from oracle import oracle as O
+    off, cols = _attach(names, n, nnz)
+    key = (name, mode, terms, seed)
+    q = _W["queries"].get(key)
+    if q is None:
+        k, edges = I.PATTERNS[name]
+        zeros64, zeros32 = np.zeros(n, dtype=np.uint64), np.zeros(n, dtype=np.uint32)
+        q = O.Query(off, cols, k, edges, nsum=zeros64, hits=zeros32, mode=mode, seed=seed, terms=terms)
+        _W["queries"][key] = q
+    return q.trials(first, count)
+
+
+def test_weights_without_statistics(oracle_mod):
+    """f_uniform and T[F1]-only f_approx read neither nsum nor the clustering hits: the
+    oracle's trials are the same with the true statistics and with zeros."""
+    off, cols = I.rmat_graph(9, 16, seed=11)
+    nsum, hits = oracle_mod.graph_stats(off, cols, 1)
+    z64, z32 = np.zeros_like(nsum), np.zeros_like(hits)
+    for name, mode, terms, _ in CASES:
+        k, edges = I.PATTERNS[name]
+        a = oracle_mod.Query(off, cols, k, edges, nsum=nsum, hits=hits, mode=mode, seed=4, terms=terms).trials(0, 500)
+        b = oracle_mod.Query(off, cols, k, edges, nsum=z64, hits=z32, mode=mode, seed=4, terms=terms).trials(0, 500)
+        for x, y in zip(a, b):
+            assert (x == y).all(), name
+
+
+@pytest.mark.gpu
+def test_int64_entry_positions_bit_exact():
+    from tests.conftest import has_gpu
+    if not has_gpu():
+        pytest.skip("needs a CUDA device")
+    import psutil
+    if psutil.virtual_memory().available < (40 << 30):
+        pytest.skip("needs 40 GB of free host memory for the 9.2 GB graph in shared memory")
+    import torch
+    from oracle import oracle as O
+    O.build()
+    from paper_2601_01388_b300 import build
+    build.build()
+    from paper_2601_01388_b300 import agis
+
+    n = N_VERTICES
+    procs = max(2, min(16, len(os.sched_getaffinity(0))))
+    pool = mp.get_context("spawn").Pool(procs)
+    shm = []
+    try:
+        blocks = [(n, u0, min(n, u0 + BLOCK)) for u0 in range(0, n, BLOCK)]
+        off = np.zeros(n + 1, dtype=np.int64)
+        for (_, u0, u1), c in zip(blocks, pool.starmap(_count_rows, blocks)):
+            off[u0 + 1:u1 + 1] = c
+        np.cumsum(off, out=off)
+        nnz = int(off[-1])
+        assert nnz > 2 ** 31 + 2 ** 27, nnz
+        for nbytes in (off.nbytes, 4 * nnz):
+            shm.append(shared_memory.SharedMemory(create=True, size=nbytes))
+        names = [s.name for s in shm]
+        s_off = np.ndarray(off.shape, dtype=np.int64, buffer=shm[0].buf)
+        s_off[:] = off
+        s_cols = np.ndarray((nnz,), dtype=np.int32, buffer=shm[1].buf)
+        pool.starmap(_fill_rows, [(names, n, nnz, u0, u1) for _, u0, u1 in blocks])
+
+        # the oracle's trials, split over the pool
+        oracle = {}
+        jobs, keys = [], []
+        for name, mode, terms, count in CASES:
+            step = -(-count // procs)
+            for first in range(0, count, step):
+                jobs.append((names, n, nnz, name, mode, terms, 17, first, min(step, count - first)))
+                keys.append((name, mode, terms))
+        for key, res in zip(keys, pool.starmap(_oracle_trials, jobs)):
+            oracle.setdefault(key, []).append(res)
+        oracle = {k: [np.concatenate([r[j] for r in v]) for j in range(4)] for k, v in oracle.items()}
+
+        torch.cuda.set_device(0)
+        ctx = agis.Context(0)
+        g = agis.Graph(ctx, s_off, s_cols, validate=True)
+        info = g.info()
+        assert info["nnz"] == nnz and info["nv"] == n
+        g.preprocess(1, 2.0 ** -10)
+        policies = [("default", None), ("partial row prefix", 4 << 30)]
+        for label, rp_bytes in policies:
+            if rp_bytes:
+                g.set_memory_policy(row_prefix_bytes=rp_bytes)
+            for name, mode, terms, count in CASES:
+                p = agis.Pattern(*I.PATTERNS[name])
+                opts = agis.default_opts(mode=mode, terms=terms, seed=17)
+                emb, hit, x, sec = agis.dump_trials(g, p, opts, 0, count)
+                oe, oh, ox, osec = oracle[(name, mode, terms)]
+                where = f"{name} mode {mode} terms {terms}, {label}"
+                assert (emb == oe).all(), where
+                assert (hit == oh).all(), where
+                assert (x == ox).all(), where
+                assert (sec == osec).all(), where
+                assert hit.sum() > count // 4, where        # most trials complete on this dense graph
+            g.drop_tables()
+        g.close()
+        ctx.close()
+        torch.cuda.empty_cache()
+    finally:
+        pool.terminate()
+        for s in shm:
+            s.close()
+            s.unlink()

@@ -98,7 +98,7 @@ def compare_dumps(agis, oracle_mod, off, cols, g, nsum, hits, name, mode, first,
     emb, hit, x, sec = agis.dump_trials(g, p, opts, first, count)
     q = oracle_mod.Query(off, cols, k, edges, nsum=nsum, hits=hits, c_min=CMIN, mode=mode, seed=seed)
     oemb, ohit, ox, osec = q.trials(first, count)
-    bad = np.nonzero((emb != oemb).any(axis=1) | (hit != ohit) | (x != ox) | (sec != osec))[0]
+    bad = np.nonzero((emb != oemb).any(axis=1) | (hit != ohit) | (x != ox) | (sec != osec).any(axis=1))[0]
     assert len(bad) == 0, (name, mode, int(bad[0]), emb[bad[0]], oemb[bad[0]], x[bad[0]], ox[bad[0]],
                            sec[bad[0]], osec[bad[0]])
     return hit
@@ -150,6 +150,7 @@ def test_fixed_budget_sums(agis, oracle_mod, graphs, name, mode):
     q = oracle_mod.Query(off, cols, k, edges, nsum=nsum, hits=hits, c_min=CMIN, mode=mode, seed=3)
     s = q.sums(0, n)
     assert r["trials"] == n and r["hits"] == s["hits"] and r["sectors"] == s["sectors"]
+    assert r["sectors_streamed"] == s["sectors_streamed"] and r["sectors_survey"] == s["sectors_survey"]
     assert r["sum_x"] == pytest.approx(s["sum_x"], rel=REL, abs=0)
     assert r["sum_x2"] == pytest.approx(s["sum_x2"], rel=REL, abs=0)
 
@@ -165,6 +166,7 @@ def test_adaptive_matches_oracle(agis, oracle_mod, graphs, name):
     o = q.estimate(eps=0.05, delta=0.05, chunk=4096, min_trials=4096, max_trials=1 << 21)
     assert r["trials"] == o["trials"] and r["converged"] == o["converged"] == 1
     assert r["hits"] == o["hits"] and r["sectors"] == o["sectors"]
+    assert r["sectors_streamed"] == o["sectors_streamed"] and r["sectors_survey"] == o["sectors_survey"]
     assert r["estimate"] == pytest.approx(o["mean"], rel=REL)
     assert r["eps_hat"] == pytest.approx(o["eps_hat"], rel=1e-6)
 
@@ -179,7 +181,8 @@ def test_batch_equals_single(agis, graphs):
     single = [agis.estimate(g, p, o) for p, o in zip(pats, opts)]
     batch = agis.estimate_batch(g, pats, opts)
     for a, b in zip(single, batch):
-        for key in ("trials", "hits", "sectors", "converged", "sum_x", "sum_x2", "estimate"):
+        for key in ("trials", "hits", "sectors", "sectors_streamed", "sectors_survey", "converged", "sum_x",
+                    "sum_x2", "estimate"):
             assert a[key] == b[key], key
 
 
@@ -190,15 +193,17 @@ def test_sample_device_tiles(agis, oracle_mod, graphs):
     p = agis.Pattern(k, edges)
     opts = agis.default_opts(mode=0, seed=9)
     ntiles = 37
-    out = torch.zeros(ntiles * 4, dtype=torch.int64, device="cuda")
+    out = torch.zeros(ntiles * agis.TILE_WORDS, dtype=torch.int64, device="cuda")
     agis.sample_device(g, p, opts, 2048, ntiles, out.data_ptr())
     torch.cuda.synchronize()
-    h, sec, sx, sx2 = agis.tile_sums(out.cpu().numpy().view(np.uint64))
+    ts = agis.tile_sums(out.cpu().numpy().view(np.uint64))
+    h, sec, sx, sx2 = ts["hits"], ts["sectors"], ts["sum_x"], ts["sum_x2"]
     q = oracle_mod.Query(off, cols, k, edges, nsum=nsum, hits=hits, c_min=CMIN, mode=0, seed=9)
     T = agis.TILE
     for t in (0, 17, 36):
         s = q.sums(2048 + T * t, T)
         assert h[t] == s["hits"] and sec[t] == s["sectors"]
+        assert ts["streamed"][t] == s["sectors_streamed"] and ts["survey"][t] == s["sectors_survey"]
         assert sx[t] == pytest.approx(s["sum_x"], rel=REL, abs=0)
         assert sx2[t] == pytest.approx(s["sum_x2"], rel=REL, abs=0)
 

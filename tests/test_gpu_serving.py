@@ -56,7 +56,7 @@ def queries(agis, n=12):
     return out
 
 
-KEYS = ("trials", "hits", "sectors", "converged", "sum_x", "sum_x2", "estimate")
+KEYS = ("trials", "hits", "sectors", "sectors_streamed", "sectors_survey", "converged", "sum_x", "sum_x2", "estimate")
 
 
 def test_served_equals_alone_and_batched(agis, setup):
@@ -78,6 +78,35 @@ def test_served_equals_alone_and_batched(agis, setup):
             assert a[k] == b[k] == c[k], k
     assert st["completed"] == len(qs)
     assert 1 <= st["peak_slots"] <= 5
+
+
+def test_continuous_admission_overlaps(agis, setup):
+    """A query that arrives while another is on the GPU joins a later epoch while the
+    first is still running (their epoch ranges overlap), finishes first, and both
+    results equal what each gives alone."""
+    ctx, g = setup
+    long_q = (agis.Pattern(*I.PATTERNS["4-clique"]), agis.default_opts(mode=0, seed=71, eps=0.0, max_trials=1 << 23))
+    short_q = (agis.Pattern(*I.PATTERNS["triangle"]),
+               agis.default_opts(mode=0, seed=72, eps=0.0, max_trials=1 << 16))
+    alone = [agis.estimate(g, p, o) for p, o in (long_q, short_q)]
+    srv = agis.Server(g, 8 << 30, 4)
+    tl = srv.submit(*long_q)
+    t0 = time.time()
+    while srv.stats()["epochs"] < 2:             # the long query is on the GPU
+        assert time.time() - t0 < 60
+        time.sleep(0.0005)
+    ts = srv.submit(*short_q)
+    rl, rs = wait_all(srv, [tl, ts])
+    st = srv.stats()
+    srv.close()
+    assert rl["admit_epoch"] == 0
+    assert rl["admit_epoch"] < rs["admit_epoch"] < rl["finish_epoch"]     # admitted mid-flight
+    assert rs["finish_epoch"] < rl["finish_epoch"]
+    for a, c in zip(alone, (rl, rs)):
+        for k in KEYS:
+            assert a[k] == c[k], k
+    assert st["epochs"] >= rl["finish_epoch"] + 1
+    assert 0.0 < st["gpu_busy_s"] <= st["busy_span_s"]
 
 
 def test_admission_by_memory(agis, setup):

@@ -62,12 +62,13 @@ def test_multi_tile_items_keep_tile_sums(agis):
         o = agis.default_opts(mode=mode, seed=12, eps=0.0, max_trials=n, chunk_trials=n)
         r = agis.estimate(g, p, o)
         ntiles = n // agis.TILE
-        out = torch.zeros(ntiles * 4, dtype=torch.int64, device="cuda")
+        out = torch.zeros(ntiles * agis.TILE_WORDS, dtype=torch.int64, device="cuda")
         agis.sample_device(g, p, o, 0, ntiles, out.data_ptr())
         torch.cuda.synchronize()
-        h, sec, sx, sx2 = agis.tile_sums(out.cpu().numpy().view(np.uint64))
+        ts = agis.tile_sums(out.cpu().numpy().view(np.uint64))
         acc = 0.0
-        for v in sx:
+        for v in ts["sum_x"]:
             acc += float(v)
-        assert r["trials"] == n and r["hits"] == int(h.sum()) and r["sectors"] == int(sec.sum())
+        assert r["trials"] == n and r["hits"] == int(ts["hits"].sum()) and r["sectors"] == int(ts["sectors"].sum())
+        assert r["sectors_streamed"] == int(ts["streamed"].sum()) and r["sectors_survey"] == int(ts["survey"].sum())
         assert r["sum_x"] == acc

@@ -90,3 +90,19 @@ def test_no_device_gives_cuda_error(agis):
     with pytest.raises(agis.AgisError) as e:
         agis.Context(0)
     assert e.value.status == agis.ERR_CUDA
+
+
+def test_layout_constants_match_header(agis):
+    """The binding's tile layout and result struct follow include/agis.h."""
+    import ctypes
+    text = open(os.path.join(ROOT, "include", "agis.h")).read()
+    assert int(re.search(r"#define AGIS_TILE_WORDS (\d+)", text).group(1)) == agis.TILE_WORDS
+    body = re.search(r"typedef struct \{([^}]*)\} agis_result;", text).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = []
+    for decl in body.split(";"):
+        words = decl.split()
+        if words:
+            fields += [n.strip() for n in " ".join(words[1:]).split(",")]
+    assert fields == [f for f, _ in agis.Result._fields_]
+    assert ctypes.sizeof(agis.Result) == 120     # 15 eight-byte slots, no padding

@@ -383,6 +383,9 @@ def test_sector_model_restated(oracle_mod, name, mode):
     # merge and one search per scanned entry, one q per candidate where weights are
     # read.  Weights are read under f_approx except on a later step whose
     # configuration has no F1, I1 or F2 term (equal weights on S_tau).
+    # Column 1 is the streamed part (the scan and the rows read once by a merge);
+    # column 2 the plain count: a search per scanned entry in every other row and
+    # the weights of every step D(i) puts under f_approx.
     off, cols = I.rmat_graph(8, 8, seed=9)
     k, edges = I.PATTERNS[name]
     q = oracle_mod.Query(off, cols, k, edges, mode=mode, seed=5)
@@ -395,25 +398,36 @@ def test_sector_model_restated(oracle_mod, name, mode):
     for t in range(len(emb)):
         tau = emb[t]
         want = _sec_search(nv + 1, 8) + (1 if info["use_approx"][0] else 0)
+        streamed, plain = 0, want
         for i in range(1, k):
             reads = info["use_approx"][i] and any(info["cfg"][i][1:])
             rows = [int(tau[j]) for j in back[i]]
             if len(rows) == 1:
                 d = int(deg[rows[0]])
-                want += 1 + (i - 1) * _sec_search(d, 4) + ((_sec_search(d, 8) + 1) if reads else 0) + 1
+                base = 1 + (i - 1) * _sec_search(d, 4) + 1
+                want += base + ((_sec_search(d, 8) + 1) if reads else 0)
+                plain += base + ((_sec_search(d, 8) + 1) if info["use_approx"][i] else 0)
             else:
                 ds = [int(deg[u]) for u in rows]
                 a = ds.index(min(ds))
-                want += len(rows) + -(-4 * ds[a] // 32)
+                scan = -(-4 * ds[a] // 32)
+                want += len(rows) + scan
+                plain += len(rows) + scan
+                streamed += scan
                 for b, m in enumerate(ds):
                     if b != a:
-                        want += min(-(-4 * max(m, 1) // 32), ds[a] * _sec_search(m, 4))
+                        merge, search = -(-4 * max(m, 1) // 32), ds[a] * _sec_search(m, 4)
+                        want += min(merge, search)
+                        streamed += merge if merge < search else 0
+                        plain += search
+                S = set.intersection(*[adj[u] for u in rows]) - set(int(v) for v in tau[:i])
                 if reads:
-                    S = set.intersection(*[adj[u] for u in rows]) - set(int(v) for v in tau[:i])
                     want += len(S)
+                if info["use_approx"][i]:
+                    plain += len(S)
             if tau[i] < 0:
                 break
-        assert sec[t] == want, (t, list(tau))
+        assert list(sec[t]) == [want, streamed, plain], (t, list(tau))
 
 
 # ---------------------------------------------------------------- sampler (Alg. 3, Thm. 2)

@@ -155,7 +155,7 @@ def test_oriented_trials_bit_exact(agis, oracle_mod, oriented, gname, name):
             q = oracle_mod.Query(oo, oc, k, edges, nsum=nsum, hits=hits, c_min=CMIN, mode=mode, seed=9,
                                  oriented=True, anchor=bool(anchor))
             oemb, ohit, ox, osec = q.trials(1000, 2100)
-            bad = np.nonzero((emb != oemb).any(axis=1) | (hit != ohit) | (x != ox) | (sec != osec))[0]
+            bad = np.nonzero((emb != oemb).any(axis=1) | (hit != ohit) | (x != ox) | (sec != osec).any(axis=1))[0]
             assert len(bad) == 0, (name, mode, anchor, int(bad[0]))
 
 
