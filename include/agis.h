@@ -47,7 +47,8 @@ typedef enum {
     AGIS_ERR_PATTERN = -5,  /* pattern violates the conventions above                   */
     AGIS_ERR_TIMEOUT = -6,  /* reserved: no device loop of this library waits on another agent */
     AGIS_ERR_BUSY = -7,     /* server: result not ready yet, or admission refused       */
-    AGIS_ERR_STATE = -8     /* call not valid in the handle's current state             */
+    AGIS_ERR_STATE = -8,    /* call not valid in the handle's current state             */
+    AGIS_ERR_IO = -9        /* a file could not be read or written, or is not a table file */
 } agis_status;
 
 /* Distribution per step: AUTO = the decision function D^pi with threshold beta
@@ -204,6 +205,43 @@ int agis_graph_is_oriented(const agis_graph *g);
 int agis_graph_set_memory_policy(agis_graph *g, uint64_t row_prefix_bytes, uint64_t bitmap_bytes,
                                  int64_t bitmap_min_degree, uint32_t list_entries);
 
+/* ---- preprocessing cache ---------------------------------------------------
+ * The System Overview runs the preprocessor only for a graph that has not been
+ * preprocessed yet; these calls keep that work across processes.
+ * agis_graph_save_tables: writes the graph's Sec. 4.4 statistics (nsum, hits, the
+ * probe seed and c_min of the last agis_graph_preprocess) and every cached f_approx
+ * weight table (q, the vertex prefix, the full row prefix; a row prefix of only the
+ * highest-degree rows is left out) to the file `path` (written to path.tmp, then
+ * renamed).  Layout: the magic "AGISTAB1", uint32 version 1, uint32 table count,
+ * int64 nv, int64 nnz, uint64 fingerprint (agis_graph_fingerprint), uint64 seed,
+ * double c_min, nsum[nv] uint64, hits[nv] uint32, then per table int32 cfg[4], int32
+ * shift, uint32 flags (bit 0 vertex prefix, bit 1 row prefix), uint64 total, q[nv],
+ * then prefix[nv] and row_prefix[nnz] as flagged; all little-endian uint64 arrays.
+ * Errors: ARG, STATE (not preprocessed), NOMEM, CUDA, IO. */
+int agis_graph_save_tables(agis_graph *g, const char *path);
+
+/* agis_graph_load_tables: reads such a file into g, which must hold the same CSR
+ * (same nv, nnz and fingerprint, else GRAPH and g is unchanged): the statistics
+ * replace any earlier preprocessing (hub bitmaps are rebuilt from the graph), cached
+ * tables are replaced by the file's, and estimates then give exactly the results of
+ * the graph the file was saved from.  A saved row prefix that the current memory
+ * policy does not allow in full is skipped (rebuilt on demand as a partial one).  If
+ * a table cannot be read the statistics stay loaded and no table is kept.
+ * Errors: ARG, GRAPH, NOMEM, CUDA, IO. */
+int agis_graph_load_tables(agis_graph *g, const char *path);
+
+/* agis_graph_fingerprint: the 64-bit CSR fingerprint that ties a table file to its
+ * graph: the wrapping sum over entries i < nnz of m(i * G XOR cols[i]) plus the sum
+ * over v <= nv of m(v * G XOR off[v] XOR S), with m SplitMix64's output function,
+ * G = 0x9E3779B97F4A7C15 and S = 0xD1B54A32D192ED03 (uint64 arithmetic, cols[i]
+ * taken as an unsigned 32-bit value).  Errors: ARG, CUDA. */
+int agis_graph_fingerprint(agis_graph *g, uint64_t *fingerprint);
+
+/* agis_tables_file_info: reads only the header of a table file (host only, no
+ * device needed).  Any output pointer may be NULL.  Errors: ARG, IO. */
+int agis_tables_file_info(const char *path, int64_t *nv, int64_t *nnz, uint64_t *fingerprint,
+                          int32_t *n_tables);
+
 /* agis_graph_drop_tables: frees every cached weight table (they are rebuilt on
  * demand). */
 int agis_graph_drop_tables(agis_graph *g);
@@ -306,20 +344,25 @@ int agis_prepare(agis_graph *g, const agis_pattern *p, const agis_opts *opts);
 
 /* agis_prefix_sum_u64_noalloc: out[i] = in[0] + ... + in[i] for i < n (uint64,
  * wrapping), the same scan that builds the weight tables' prefix sums, for callers
- * that cannot call cudaMalloc -- code running while a CUDA graph is captured, code
- * inside a custom allocator or host callback that must not re-enter the CUDA
- * allocator, or a service whose device memory is already fully reserved by a pool.
- * The paper has no counterpart; this is a library service.
- * in and out are device pointers on the current device (they may not overlap);
- * the work is enqueued on cuda_stream (NULL = legacy default stream) and nothing is
- * allocated or freed: the tile-sum scratch is a file-scope device array of 65536
- * uint64 (512 KiB), held by every device that loads the library until the process
- * exits.  So n is at most 65536 * 2048 = 134217728; larger n returns ARG.
- * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture.  All calls share the one array: calls whose work overlaps on the GPU
- * (other streams, or other host threads) race on it and must be serialised by the
- * caller.  Errors: ARG (n < 0, n too large, null pointer), CUDA. */
+ * that cannot call cudaMalloc: a custom device allocator or memory-pool hook that
+ * must not re-enter the CUDA allocator, a service whose device memory a pool already
+ * holds in full, or latency-critical code that avoids cudaMalloc because it can
+ * block and synchronise the device.  The paper has no counterpart; this is a
+ * library service.
+ * in and out are device pointers of the context current on the calling thread
+ * (they may not overlap); the work is enqueued on cuda_stream (NULL = legacy default
+ * stream) and nothing is allocated or freed: the tile-sum scratch is a file-scope
+ * device array of 65536 uint64 (512 KiB), held by every device that loads the
+ * library until the process exits.  So n is at most 65536 * 2048 = 134217728;
+ * larger n returns ARG.
+ * The first call in a CUDA context looks up the array's device address (once per
+ * context; a reset device or another context is looked up again); make that first
+ * call before any stream capture.  All calls share the one array, which keeps the
+ * last call's tile sums (each call writes every entry it reads first): calls whose
+ * work overlaps on the GPU (other streams, or other host threads) race on it and
+ * must be serialised by the caller.  A launch error, or an error still pending from
+ * earlier work on this thread, is returned as CUDA.
+ * Errors: ARG (n < 0, n too large, null pointer), CUDA. */
 int agis_prefix_sum_u64_noalloc(const uint64_t *in, int64_t n, uint64_t *out, void *cuda_stream);
 
 /* agis_probe_random_read: enqueues (on cuda_stream) about `reads` independent reads,

@@ -21,8 +21,8 @@ if not os.path.exists(LIB_PATH):
 
 _lib = C.CDLL(LIB_PATH)
 
-OK, ERR_ARG, ERR_NOMEM, ERR_CUDA, ERR_GRAPH, ERR_PATTERN, ERR_TIMEOUT, ERR_BUSY, ERR_STATE = \
-    0, -1, -2, -3, -4, -5, -6, -7, -8
+OK, ERR_ARG, ERR_NOMEM, ERR_CUDA, ERR_GRAPH, ERR_PATTERN, ERR_TIMEOUT, ERR_BUSY, ERR_STATE, ERR_IO = \
+    0, -1, -2, -3, -4, -5, -6, -7, -8, -9
 MODE_AUTO, MODE_APPROX, MODE_UNIFORM = 0, 1, 2
 
 EXPORTS = [
@@ -32,7 +32,8 @@ EXPORTS = [
     "agis_pattern_create", "agis_pattern_info", "agis_pattern_decide", "agis_pattern_free",
     "agis_estimate", "agis_estimate_batch", "agis_autotune", "agis_dump_trials", "agis_sample_device",
     "agis_prepare", "agis_tile_trials", "agis_z_of_delta", "agis_kernel_launches", "agis_prefix_sum_u64_noalloc", "agis_probe_random_read", "agis_step_timers", "agis_server_create", "agis_server_submit", "agis_server_poll",
-    "agis_server_stats", "agis_server_destroy",
+    "agis_server_stats", "agis_server_destroy", "agis_graph_save_tables", "agis_graph_load_tables",
+    "agis_graph_fingerprint", "agis_tables_file_info",
 ]
 
 
@@ -98,6 +99,10 @@ _sig = {
     "agis_server_poll": ([VP, C.c_uint64, P(Result), P(C.c_double), P(C.c_uint64)], C.c_int),
     "agis_server_stats": ([VP, P(C.c_uint64), P(C.c_uint64), P(C.c_int32), P(C.c_double), P(C.c_double)], C.c_int),
     "agis_server_destroy": ([VP], C.c_int),
+    "agis_graph_save_tables": ([VP, C.c_char_p], C.c_int),
+    "agis_graph_load_tables": ([VP, C.c_char_p], C.c_int),
+    "agis_graph_fingerprint": ([VP, P(C.c_uint64)], C.c_int),
+    "agis_tables_file_info": ([C.c_char_p, P(C.c_int64), P(C.c_int64), P(C.c_uint64), P(C.c_int32)], C.c_int),
 }
 for _name, (_args, _res) in _sig.items():
     _f = getattr(_lib, _name, None)
@@ -343,6 +348,19 @@ class Graph:
     def drop_tables(self):
         _check(_lib.agis_graph_drop_tables(self.h), "agis_graph_drop_tables")
 
+    def save_tables(self, path):
+        """Writes the statistics and cached weight tables to `path` (see agis.h)."""
+        _check(_lib.agis_graph_save_tables(self.h, os.fsencode(path)), "agis_graph_save_tables")
+
+    def load_tables(self, path):
+        """Reads statistics and tables saved from a graph with the same CSR."""
+        _check(_lib.agis_graph_load_tables(self.h, os.fsencode(path)), "agis_graph_load_tables")
+
+    def fingerprint(self):
+        f = C.c_uint64()
+        _check(_lib.agis_graph_fingerprint(self.h, C.byref(f)), "agis_graph_fingerprint")
+        return f.value
+
     def close(self):
         if getattr(self, "h", None):
             _lib.agis_graph_free(self.h)
@@ -353,6 +371,14 @@ class Graph:
             self.close()
         except Exception:
             pass
+
+
+def tables_file_info(path) -> dict:
+    """Header of a table file (host only)."""
+    nv, nnz, fp, nt = C.c_int64(), C.c_int64(), C.c_uint64(), C.c_int32()
+    _check(_lib.agis_tables_file_info(os.fsencode(path), C.byref(nv), C.byref(nnz), C.byref(fp), C.byref(nt)),
+           "agis_tables_file_info")
+    return {"nv": nv.value, "nnz": nnz.value, "fingerprint": fp.value, "n_tables": nt.value}
 
 
 def estimate(graph: Graph, pattern: Pattern, opts: Opts) -> dict:

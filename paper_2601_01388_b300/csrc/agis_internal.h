@@ -14,9 +14,21 @@
 #include <unordered_map>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/agis.h"
 
 namespace agis {
+
+// An NVTX range for the scope (header-only NVTX 3: without a profiler attached a
+// push/pop costs a check of one function pointer).  Range names start with "agis:"
+// so that a profiler's launch list can be attributed to the phases of the path.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 constexpr int kMaxK = 8;
 #ifndef AGIS_TILE

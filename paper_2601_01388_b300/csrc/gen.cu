@@ -304,6 +304,7 @@ using namespace agis;
 extern "C" int agis_graph_generate_rmat(agis_ctx *ctx, int scale, int edge_factor, double a, double b, double c,
                                         uint64_t seed, agis_graph **out)
 {
+    agis::NvtxRange nvtx_range("agis:generate");
     if (!ctx || !out || scale < 1 || scale > 30 || edge_factor < 1 || !(a >= 0 && b >= 0 && c >= 0) ||
         a + b + c > 1.0)
         return AGIS_ERR_ARG;
@@ -324,6 +325,7 @@ extern "C" int agis_graph_generate_rmat(agis_ctx *ctx, int scale, int edge_facto
 extern "C" int agis_graph_generate_chunglu(agis_ctx *ctx, int64_t n, double gamma, double mean_degree,
                                            uint64_t seed, agis_graph **out)
 {
+    agis::NvtxRange nvtx_range("agis:generate");
     if (!ctx || !out || n < 2 || n > INT32_MAX || !(gamma > 1.0) || !(mean_degree > 0.0) ||
         mean_degree >= (double)n)
         return AGIS_ERR_ARG;

@@ -536,6 +536,7 @@ void free_table(WeightTable &t)
 int build_weight_table(agis_graph *g, const int32_t cfg[4], bool need_pref, bool need_rowp,
                        WeightTable **out)
 {
+    agis::NvtxRange nvtx_range("agis:tables");
     if (!g->prepped) return AGIS_ERR_STATE;
     cudaStream_t st = g->ctx->stream;
     const uint64_t key = cfg_key(cfg);
@@ -622,6 +623,7 @@ extern "C" int agis_graph_load_csr(agis_ctx *ctx, const void *offsets, int offse
                                    const int32_t *cols, int64_t nv, int64_t nnz, int on_device,
                                    int validate, agis_graph **out)
 {
+    agis::NvtxRange nvtx_range("agis:load");
     if (!ctx || !out || !offsets || (nnz > 0 && !cols) || nv < 1 || nnz < 0 || nv > INT32_MAX)
         return AGIS_ERR_ARG;
     *out = nullptr;
@@ -699,6 +701,7 @@ extern "C" int agis_graph_load_csr(agis_ctx *ctx, const void *offsets, int offse
 
 extern "C" int agis_graph_preprocess(agis_graph *g, uint64_t seed, double c_min)
 {
+    agis::NvtxRange nvtx_range("agis:preprocess");
     if (!g || !(c_min > 0.0) || c_min > 1.0) return AGIS_ERR_ARG;
     std::lock_guard<std::recursive_mutex> lk(g->mu);
     AGIS_CUDA_TRY(cudaSetDevice(g->ctx->device));
@@ -834,6 +837,7 @@ extern "C" int agis_graph_copy_csr(const agis_graph *g, int64_t *off, int32_t *c
 
 extern "C" int agis_graph_orient(agis_graph *g, agis_graph **out)
 {
+    agis::NvtxRange nvtx_range("agis:orient");
     if (!g || !out) return AGIS_ERR_ARG;
     *out = nullptr;
     if (g->oriented) return AGIS_ERR_STATE;
@@ -894,13 +898,13 @@ extern "C" int agis_graph_is_oriented(const agis_graph *g)
 }
 
 // ---------------------------------------------------------------- prefix sum without allocation
-// Some callers cannot call cudaMalloc: code running while a CUDA graph is being
-// captured (an allocation is not a capturable operation), code inside a host
-// callback or a custom allocator that must not re-enter the CUDA allocator, and
-// services whose device memory is already fully reserved by a pool allocator.  For
-// them this variant of the prefix-sum scan keeps its tile-sum scratch in a
-// file-scope device array instead of allocating it.  The array exists once on every
-// device that loads this library and stays allocated until the process exits.
+// Some callers cannot call cudaMalloc: a custom device allocator or memory-pool hook
+// that must not re-enter the CUDA allocator, a service whose device memory a pool
+// already holds in full (so an allocation would fail), and latency-critical code
+// that avoids cudaMalloc because it can block and synchronise the device.  For them
+// this variant of the prefix-sum scan keeps its tile-sum scratch in a file-scope
+// device array instead of allocating it.  The array exists once on every device that
+// loads this library and stays allocated until the process exits.
 
 namespace agis {
 namespace {
@@ -910,23 +914,58 @@ constexpr int64_t kNoAllocMaxN = kNoAllocMaxTiles * kScanTile;
 
 static __device__ __align__(256) uint64_t g_noalloc_tile_sums[kNoAllocMaxTiles];
 
-constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
-uint64_t *g_noalloc_ptr[kMaxDevices] = {nullptr};
+std::unordered_map<unsigned long long, uint64_t *> g_noalloc_ptr;   // context id -> array address
 
-// Device address of the scratch array on the current device, looked up once per
-// device (host code must not use the array's name as an address).
-int noalloc_scratch(int device, uint64_t **out)
+// cuCtxGetCurrent and cuCtxGetId, reached through the runtime's driver entry points
+// (the library links only the runtime).
+typedef int (*CtxGetCurrentFn)(void **);
+typedef int (*CtxGetIdFn)(void *, unsigned long long *);
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+CtxGetIdFn g_ctx_get_id = nullptr;
+
+// Unique id of the context current on this thread (0 when none is current); ids are
+// never reused within a process, so a reset device or another context gets a new one.
+int current_context_id(unsigned long long *id)
 {
-    if (device < 0 || device >= kMaxDevices) return AGIS_ERR_ARG;
-    std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_ptr[device]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_tile_sums);
-        if (e != cudaSuccess || !p) return AGIS_ERR_CUDA;
-        g_noalloc_ptr[device] = (uint64_t *)p;
+    *id = 0;
+    if (!g_ctx_get_current || !g_ctx_get_id) {
+        void *f0 = nullptr, *f1 = nullptr;
+        cudaDriverEntryPointQueryResult q0, q1;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f0, 12000, cudaEnableDefault, &q0) != cudaSuccess ||
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f1, 12000, cudaEnableDefault, &q1) != cudaSuccess ||
+            q0 != cudaDriverEntryPointSuccess || q1 != cudaDriverEntryPointSuccess || !f0 || !f1)
+            return AGIS_ERR_CUDA;
+        g_ctx_get_current = (CtxGetCurrentFn)f0;
+        g_ctx_get_id = (CtxGetIdFn)f1;
     }
-    *out = g_noalloc_ptr[device];
+    void *ctx = nullptr;
+    if (g_ctx_get_current(&ctx) != 0) return AGIS_ERR_CUDA;
+    if (ctx && g_ctx_get_id(ctx, id) != 0) return AGIS_ERR_CUDA;
+    return AGIS_OK;
+}
+
+// Device address of the scratch array in the context current on this thread, looked
+// up once per context (host code must not use the array's name as an address).
+int noalloc_scratch(uint64_t **out)
+{
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    unsigned long long id = 0;
+    int rc = current_context_id(&id);
+    if (rc != AGIS_OK) return rc;
+    if (id != 0) {
+        auto it = g_noalloc_ptr.find(id);
+        if (it != g_noalloc_ptr.end()) {
+            *out = it->second;
+            return AGIS_OK;
+        }
+    }
+    // the lookup also makes the device's primary context current when none is
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_tile_sums) != cudaSuccess || !p) return AGIS_ERR_CUDA;
+    if (id == 0 && ((rc = current_context_id(&id)) != AGIS_OK || id == 0)) return rc != AGIS_OK ? rc : AGIS_ERR_CUDA;
+    g_noalloc_ptr[id] = (uint64_t *)p;
+    *out = (uint64_t *)p;
     return AGIS_OK;
 }
 
@@ -939,10 +978,8 @@ extern "C" int agis_prefix_sum_u64_noalloc(const uint64_t *in, int64_t n, uint64
     if (n < 0 || (n > 0 && (!in || !out))) return AGIS_ERR_ARG;
     if (n > kNoAllocMaxN) return AGIS_ERR_ARG;
     if (n == 0) return AGIS_OK;
-    int device = 0;
-    AGIS_CUDA_TRY(cudaGetDevice(&device));
     uint64_t *tile_sums = nullptr;
-    int rc = noalloc_scratch(device, &tile_sums);
+    int rc = noalloc_scratch(&tile_sums);
     if (rc != AGIS_OK) return rc;
     cudaStream_t st = (cudaStream_t)cuda_stream;
     const int64_t tiles = (n + kScanTile - 1) / kScanTile;
@@ -950,11 +987,14 @@ extern "C" int agis_prefix_sum_u64_noalloc(const uint64_t *in, int64_t n, uint64
     // array needs no clearing between calls
     count_launch();
     k_scan_tile_sums<<<(unsigned)tiles, kScanThreads, 0, st>>>(in, n, tile_sums);
+    AGIS_CUDA_TRY(cudaGetLastError());
     count_launch();
     k_scan_single<<<1, kScanThreads, 0, st>>>(tile_sums, tiles);
+    AGIS_CUDA_TRY(cudaGetLastError());
     count_launch();
     k_scan_apply<<<(unsigned)tiles, kScanThreads, 0, st>>>(in, n, tile_sums, out);
-    return cuda_status(cudaGetLastError());
+    AGIS_CUDA_TRY(cudaGetLastError());
+    return AGIS_OK;
 }
 
 extern "C" int agis_graph_set_memory_policy(agis_graph *g, uint64_t row_prefix_bytes, uint64_t bitmap_bytes,

@@ -421,6 +421,7 @@ static bool any_anchor(const std::vector<QueryRun *> &runs)
 int run_epoch_direct(agis_graph *g, std::vector<QueryRun *> &runs, const std::vector<uint64_t> &ntiles,
                      size_t total)
 {
+    agis::NvtxRange nvtx_range("agis:epoch");
     LaunchBuffers &lb = g->lb;
     cudaStream_t st = g->ctx->stream;
     int rc = ensure_buffers(lb, runs.size(), total);
@@ -448,6 +449,7 @@ int enqueue_epoch_graph(agis_graph *g, LaunchBuffers &lb, const LaunchBuffers &s
                         std::vector<QueryRun *> &runs, const std::vector<uint64_t> &ntiles, size_t total,
                         cudaEvent_t start, cudaEvent_t done)
 {
+    agis::NvtxRange nvtx_range("agis:epoch");
     cudaStream_t st = g->ctx->stream;
     int rc = ensure_buffers(lb, runs.size(), total);
     if (rc != AGIS_OK) return rc;
@@ -571,6 +573,7 @@ extern "C" const char *agis_status_str(int s)
     case AGIS_ERR_TIMEOUT: return "timeout";
     case AGIS_ERR_BUSY: return "busy";
     case AGIS_ERR_STATE: return "invalid state";
+    case AGIS_ERR_IO: return "file error";
     default: return "unknown status";
     }
 }
@@ -737,6 +740,7 @@ extern "C" int agis_estimate_batch(agis_graph *g, int n, const agis_pattern *con
 extern "C" int agis_dump_trials(agis_graph *g, const agis_pattern *p, const agis_opts *opts, uint64_t first,
                                 uint64_t count, int32_t *emb, uint8_t *hit, double *x, uint64_t *sectors)
 {
+    agis::NvtxRange nvtx_range("agis:dump");
     if (!g || !p || !opts) return AGIS_ERR_ARG;
     if (count == 0) return AGIS_OK;
     std::lock_guard<std::recursive_mutex> lk(g->mu);
@@ -780,6 +784,7 @@ extern "C" int agis_dump_trials(agis_graph *g, const agis_pattern *p, const agis
 extern "C" int agis_sample_device(agis_graph *g, const agis_pattern *p, const agis_opts *opts, uint64_t first,
                                   uint64_t ntiles, uint64_t *tile_out)
 {
+    agis::NvtxRange nvtx_range("agis:sample");
     if (!g || !p || !opts || !tile_out || ntiles == 0 || ntiles > 0xffffffffull) return AGIS_ERR_ARG;
     std::lock_guard<std::recursive_mutex> lk(g->mu);
     AGIS_CUDA_TRY(cudaSetDevice(g->ctx->device));
@@ -822,6 +827,7 @@ extern "C" uint64_t agis_kernel_launches(void) { return g_launches.load(); }
 extern "C" int agis_autotune(agis_graph *g, int n, const agis_pattern *const *patterns, const agis_opts *opts,
                              uint64_t trials_per_query, int32_t *blocks_per_sm, int32_t *tiles_per_item)
 {
+    agis::NvtxRange nvtx_range("agis:autotune");
     if (!g || n <= 0 || !patterns || !opts || trials_per_query == 0) return AGIS_ERR_ARG;
     std::lock_guard<std::recursive_mutex> lk(g->mu);
     AGIS_CUDA_TRY(cudaSetDevice(g->ctx->device));

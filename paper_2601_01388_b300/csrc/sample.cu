@@ -308,6 +308,13 @@ constexpr int kGroups = AGIS_FILTER_GROUPS;
 #ifndef AGIS_MERGE_RATIO
 #define AGIS_MERGE_RATIO 0
 #endif
+// A hub row (one with a bitmap) is merged by the whole warp instead of probed entry
+// by entry while m <= AGIS_HUB_MERGE_RATIO * n: the merge reads the row once, in
+// coalesced 128-byte windows that often hit L2 (hub rows are the hot ones), where
+// the probes fetch one 32-byte bitmap sector per entry.
+#ifndef AGIS_HUB_MERGE_RATIO
+#define AGIS_HUB_MERGE_RATIO 0
+#endif
 
 // Running weights of out[0, cnt): gathers q for two windows at a time.
 __device__ __forceinline__ uint64_t weigh_list(const int32_t *out, uint32_t cnt, uint64_t *out_pw,
@@ -406,7 +413,7 @@ __device__ uint32_t filter_list(const int32_t *L, uint32_t n, const int32_t *R, 
     if (R && n >= 256 && m >= 256 && n <= 2 * cap && (!Rbits || m < (int64_t)AGIS_MERGE_RATIO * n))
         return filter_lane_merge<kWeigh>(L, n, R, m, tau_s, tau_n, out, reinterpret_cast<int32_t *>(out_pw),
                                          out_pw, cap, q, approx, W, lane);
-    if (Rbits || !R) {
+    if (!R || (Rbits && !((int64_t)m <= (int64_t)AGIS_HUB_MERGE_RATIO * (int64_t)n))) {
         // Survivor ids first: 16-byte loads of four consecutive entries per lane,
         // kGroups groups of 128 entries per iteration, so 4 * kGroups bitmap probes
         // per lane are in flight together; the survivors' weights are gathered afterwards in

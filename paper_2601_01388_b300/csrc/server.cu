@@ -289,8 +289,9 @@ void scheduler(agis_server *s)
             if (inflight.size() < 2) {
                 int rc = AGIS_OK;
                 const bool was_idle = inflight.empty();
+                const double t_enqueue = now_s();
                 queued = launch_epoch(s, inflight, rc);
-                if (queued && was_idle) span_t0 = now_s();
+                if (queued && was_idle) span_t0 = t_enqueue;
                 if (rc != AGIS_OK) {
                     for (Served *q : s->active) finish(s, q, rc);
                     s->active.clear();

@@ -106,7 +106,8 @@ def test_continuous_admission_overlaps(agis, setup):
         for k in KEYS:
             assert a[k] == c[k], k
     assert st["epochs"] >= rl["finish_epoch"] + 1
-    assert 0.0 < st["gpu_busy_s"] <= st["busy_span_s"]
+    # device time (events) within the host's busy span, up to the two clocks' skew
+    assert 0.0 < st["gpu_busy_s"] <= st["busy_span_s"] * 1.001 + 1e-4
 
 
 def test_admission_by_memory(agis, setup):

@@ -1,12 +1,12 @@
 """The allocation-free prefix sum (agis_prefix_sum_u64_noalloc).
 
-Callers that cannot call cudaMalloc -- code running under CUDA-graph capture, code
-inside a custom allocator or host callback, services whose device memory a pool
-already holds -- use this entry point: it keeps its scratch in a file-scope device
-array.  Its output is checked, twice in a row, against the prefix sums the
-existing weight-table entry point (agis_graph_weight_table) returns for the same
-input; both are exact integer scans, so they must be equal.  This file is named
-to be collected last."""
+Callers that cannot call cudaMalloc -- a custom device allocator or pool hook that
+must not re-enter the CUDA allocator, a service whose device memory a pool already
+holds in full, latency-critical code that avoids cudaMalloc's blocking -- use this
+entry point: it keeps its scratch in a file-scope device array.  Its output is
+checked, twice in a row, against the prefix sums the existing weight-table entry
+point (agis_graph_weight_table) returns for the same input; both are exact integer
+scans, so they must be equal.  This file is named to be collected last."""
 import numpy as np
 import pytest
 
