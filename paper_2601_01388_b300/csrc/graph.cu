@@ -435,11 +435,11 @@ int build_hub_bitmaps(agis_graph *g)
     AGIS_CUDA_TRY(cudaMalloc(&g->hub_id, sizeof(int32_t) * (size_t)g->nv));
     AGIS_CUDA_TRY(cudaMemcpyAsync(g->hub_id, hub_id.data(), sizeof(int32_t) * (size_t)g->nv, cudaMemcpyHostToDevice, st));
     if (!hubs.empty()) {
-        AGIS_CUDA_TRY(cudaMalloc(&g->hub_bits, per_hub * hubs.size()));
-        AGIS_CUDA_TRY(cudaMemsetAsync(g->hub_bits, 0, per_hub * hubs.size(), st));
         int32_t *d_hubs = nullptr;
         AGIS_CUDA_TRY(cudaMallocAsync(&d_hubs, sizeof(int32_t) * hubs.size(), st));
         AGIS_CUDA_TRY(cudaMemcpyAsync(d_hubs, hubs.data(), sizeof(int32_t) * hubs.size(), cudaMemcpyHostToDevice, st));
+        AGIS_CUDA_TRY(cudaMalloc(&g->hub_bits, per_hub * hubs.size()));
+        AGIS_CUDA_TRY(cudaMemsetAsync(g->hub_bits, 0, per_hub * hubs.size(), st));
         count_launch();
         k_hub_bitmaps<<<(unsigned)hubs.size(), 256, 0, st>>>(g->off, g->cols, d_hubs, g->hub_words, g->hub_bits);
         AGIS_CUDA_TRY(cudaGetLastError());

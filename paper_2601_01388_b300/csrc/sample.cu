@@ -23,9 +23,10 @@
 #include "philox.cuh"
 
 // Resident CTAs per SM the register allocation is sized for (the build may
-// override it; the autotuner then picks up to this many).
+// override it; the autotuner then picks up to this many).  Five (40 warps, 48
+// registers) ran 2% faster than four and 2% faster than six on the benchmark graph.
 #ifndef AGIS_MIN_BLOCKS
-#define AGIS_MIN_BLOCKS 4
+#define AGIS_MIN_BLOCKS 5
 #endif
 
 namespace agis {
@@ -228,12 +229,19 @@ struct TrialOut {
     int hit;
 };
 
+// A backward row of a step: where it starts in cols, its length, its neighbour
+// bitmap (null if none).  Kept per warp in shared memory (the values are the same on
+// every lane), so they take neither registers nor local memory.
+struct RowRef {
+    int64_t start, len;
+    const uint32_t *bits;
+};
+
 // One window of the intersection scan: entry `idx` of the anchor row for this
 // lane; returns the lane's candidate weight (0 if not in S) and sets ok / x.
 __device__ __forceinline__ uint64_t window_weight(const GraphView &g, const DevStep &S,
                                                   const int32_t *tau_s, int i, int64_t a_start,
-                                                  int64_t da, int64_t idx, const int64_t *o_start,
-                                                  const int64_t *o_len, const uint32_t *const *o_bits,
+                                                  int64_t da, int64_t idx, const RowRef *rows,
                                                   int n_other, bool &ok, int32_t &x)
 {
     ok = idx < da;
@@ -242,7 +250,7 @@ __device__ __forceinline__ uint64_t window_weight(const GraphView &g, const DevS
         for (int j = 0; j < i; ++j) ok &= (x != tau_s[j]);
     }
     for (int o = 0; o < n_other; ++o) {
-        if (ok) ok = o_bits[o] ? bit_test(o_bits[o], x) : row_find(g.cols + o_start[o], o_len[o], x) >= 0;
+        if (ok) ok = rows[o].bits ? bit_test(rows[o].bits, x) : row_find(g.cols + rows[o].start, rows[o].len, x) >= 0;
     }
     if (!ok) return 0;
     return S.approx ? __ldg(S.q + x) : 1u;
@@ -575,7 +583,7 @@ __device__ __forceinline__ uint64_t closing_sectors(const GraphView &g, const De
 
 template <bool kAnchor>
 __device__ TrialOut run_trial(const GraphView &g, const DevQuery &Q, uint64_t t, int32_t *tau_s,
-                              const WarpSets &ws, const uint64_t *top, uint64_t *wsec, int lane)
+                              const WarpSets &ws, const uint64_t *top, uint64_t *wsec, RowRef *rows, int lane)
 {
     TrialOut out{0.0, 0, 0, 0, 0};
     double X = 1.0;
@@ -676,26 +684,34 @@ __device__ TrialOut run_trial(const GraphView &g, const DevQuery &Q, uint64_t t,
         } else {
             // ---- several backward neighbours (or one, with no row-prefix table):
             //      intersect, anchored at the shortest row
-            int64_t o_start[kMaxK - 1], o_len[kMaxK - 1];
-            const uint32_t *o_bits[kMaxK - 1];
-            int ai = 0;
-            int64_t a_start = 0, da = -1;
-            for (int b = 0; b < S.nb; ++b) {
-                const int32_t u = tau_s[S.back[b]];
-                const int64_t s0 = __ldg(g.off + u), len = __ldg(g.off + u + 1) - s0;
-                if (da < 0 || len < da) { da = len; ai = b; a_start = s0; }
+            // lane b reads backward row b; the anchor is the shortest row, the first in
+            // backward order on ties; the other rows go to the warp's rows[] in order
+            int64_t my_start = 0, my_len = INT64_MAX;
+            const uint32_t *my_bits = nullptr;
+            if (lane < S.nb) {
+                const int32_t u = tau_s[S.back[lane]];
+                my_start = __ldg(g.off + u);
+                my_len = __ldg(g.off + u + 1) - my_start;
+                my_bits = bits_of(g, u);
             }
-            int n_other = 0;
+            int64_t da = my_len;
+            int ai = lane;
+            for (int o = 16; o > 0; o >>= 1) {
+                const int64_t ol = __shfl_xor_sync(kFull, da, o);
+                const int oa = __shfl_xor_sync(kFull, ai, o);
+                if (ol < da || (ol == da && oa < ai)) { da = ol; ai = oa; }
+            }
+            const int64_t a_start = __shfl_sync(kFull, my_start, ai);
             uint64_t search_sec = 0, merge_st = 0, search_sv = 0;
-            for (int b = 0; b < S.nb; ++b) {
-                if (b == ai) continue;
-                const int32_t u = tau_s[S.back[b]];
-                o_start[n_other] = __ldg(g.off + u);
-                o_len[n_other] = __ldg(g.off + u + 1) - o_start[n_other];
-                o_bits[n_other] = bits_of(g, u);
-                search_sec += row_check_sectors(da, o_len[n_other], merge_st, search_sv);
-                ++n_other;
+            if (lane < S.nb && lane != ai) {
+                rows[lane - (lane > ai ? 1 : 0)] = RowRef{my_start, my_len, my_bits};
+                search_sec = row_check_sectors(da, my_len, merge_st, search_sv);
             }
+            search_sec = warp_sum_u64(search_sec);
+            merge_st = warp_sum_u64(merge_st);
+            search_sv = warp_sum_u64(search_sv);
+            const int n_other = S.nb - 1;
+            __syncwarp();
             // an anchor draw filters only trajectory members here; the other rows are
             // checked for the drawn vertex alone
             const int n_filter = anch ? 0 : n_other;
@@ -734,9 +750,9 @@ __device__ TrialOut run_trial(const GraphView &g, const DevQuery &Q, uint64_t t,
                         m = __ldg(g.off + u + 1) - __ldg(g.off + u);
                         Rb = bits_of(g, u);
                     } else if (n_filter > 0) {
-                        R = g.cols + o_start[pss];
-                        m = o_len[pss];
-                        Rb = o_bits[pss];
+                        R = g.cols + rows[pss].start;
+                        m = rows[pss].len;
+                        Rb = rows[pss].bits;
                     }
                     // The last pass forms the running weights of an f_approx list.  A
                     // position draw needs survivor ids alone, but only a query none of
@@ -799,8 +815,8 @@ __device__ TrialOut run_trial(const GraphView &g, const DevQuery &Q, uint64_t t,
                 uint64_t wtv[U];
 #pragma unroll
                 for (int u = 0; u < U; ++u)
-                    wtv[u] = window_weight(g, S, tau_s, i, a_start, da, (w0 + u) * 32 + lane, o_start,
-                                           o_len, o_bits, n_filter, okv[u], xv[u]);
+                    wtv[u] = window_weight(g, S, tau_s, i, a_start, da, (w0 + u) * 32 + lane, rows,
+                                           n_filter, okv[u], xv[u]);
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     const int64_t w = w0 + u;
@@ -838,7 +854,7 @@ __device__ TrialOut run_trial(const GraphView &g, const DevQuery &Q, uint64_t t,
                     bool ok;
                     int32_t x;
                     const uint64_t wt = window_weight(g, S, tau_s, i, a_start, da, w * 32 + lane,
-                                                      o_start, o_len, o_bits, n_filter, ok, x);
+                                                      rows, n_filter, ok, x);
                     const uint64_t incl = warp_incl_scan(wt, lane);
                     const uint64_t wtot = __shfl_sync(kFull, incl, 31);
                     if (run2 + wtot > r) {
@@ -890,6 +906,7 @@ __global__ void __launch_bounds__(kBlock, AGIS_MIN_BLOCKS) sample_kernel(GraphVi
     __shared__ double red2[kBlock];
     __shared__ int32_t tau_s[kWarps][kMaxK];
     __shared__ uint64_t s_wsec[kWarps][2];
+    __shared__ RowRef s_rows[kWarps][kMaxK - 1];
     __shared__ uint64_t s_top[kTopSplitters];
     __shared__ uint32_t s_item, s_next, s_hits[kMaxSpan];
     __shared__ unsigned long long s_sec[kMaxSpan][3];
@@ -897,17 +914,21 @@ __global__ void __launch_bounds__(kBlock, AGIS_MIN_BLOCKS) sample_kernel(GraphVi
     __shared__ WorkItem s_it;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t n_items = *n_items_ptr;
-    WarpSets ws;
-    {
+    // the warp's candidate lists (pointers kept in shared memory: warp-uniform values)
+    __shared__ WarpSets s_ws[kWarps];
+    if (lane == 0) {
         const size_t per = (size_t)scratch_cap * 2 * (sizeof(int32_t) + sizeof(uint64_t));
         const size_t stride = (per + 255) / 256 * 256;
         char *base = scratch + stride * ((size_t)blockIdx.x * kWarps + warp);
-        ws.cap = scratch ? scratch_cap : 0;
-        ws.xs[0] = (int32_t *)base;
-        ws.xs[1] = ws.xs[0] + scratch_cap;
-        ws.pw[0] = (uint64_t *)(base + (size_t)scratch_cap * 2 * sizeof(int32_t));
-        ws.pw[1] = ws.pw[0] + scratch_cap;
+        WarpSets &w = s_ws[warp];
+        w.cap = scratch ? scratch_cap : 0;
+        w.xs[0] = (int32_t *)base;
+        w.xs[1] = w.xs[0] + scratch_cap;
+        w.pw[0] = (uint64_t *)(base + (size_t)scratch_cap * 2 * sizeof(int32_t));
+        w.pw[1] = w.pw[0] + scratch_cap;
     }
+    __syncwarp();
+    const WarpSets &ws = s_ws[warp];
     if (threadIdx.x == 0) s_query = -1;
     for (;;) {
         if (threadIdx.x == 0) {
@@ -960,7 +981,7 @@ __global__ void __launch_bounds__(kBlock, AGIS_MIN_BLOCKS) sample_kernel(GraphVi
             tt = __shfl_sync(kFull, tt, 0);
             if (tt >= it.count) break;
             const uint64_t t = it.first + tt;
-            const TrialOut r = run_trial<kAnchor>(g, sq, t, tau_s[warp], ws, s_top, s_wsec[warp], lane);
+            const TrialOut r = run_trial<kAnchor>(g, sq, t, tau_s[warp], ws, s_top, s_wsec[warp], s_rows[warp], lane);
             if (lane == 0) {
                 xs[tt] = r.x;
                 if (r.hit) atomicAdd(&s_hits[tt / kTile], 1u);

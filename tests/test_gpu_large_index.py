@@ -81,8 +81,12 @@ def test_int64_entry_positions_bit_exact():
     from tests.conftest import has_gpu
     if not has_gpu():
         pytest.skip("needs a CUDA device")
-    import psutil
-    if psutil.virtual_memory().available < (40 << 30):
+    avail = 0
+    with open("/proc/meminfo") as f:
+        for line in f:
+            if line.startswith("MemAvailable:"):
+                avail = int(line.split()[1]) << 10
+    if avail < (40 << 30):
         pytest.skip("needs 40 GB of free host memory for the 9.2 GB graph in shared memory")
     import torch
     from oracle import oracle as O
@@ -102,7 +106,7 @@ def test_int64_entry_positions_bit_exact():
             off[u0 + 1:u1 + 1] = c
         np.cumsum(off, out=off)
         nnz = int(off[-1])
-        assert nnz > 2 ** 31 + 2 ** 27, nnz
+        assert nnz > 2 ** 31 + 2 ** 26, nnz
         for nbytes in (off.nbytes, 4 * nnz):
             shm.append(shared_memory.SharedMemory(create=True, size=nbytes))
         names = [s.name for s in shm]
