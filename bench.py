@@ -81,6 +81,8 @@ def parse_args(argv=None):
     ap.add_argument("--summarize-ncu", default="",
                     help="(no GPU) turn an ncu CSV of sampler launches into the committed JSON traffic summary")
     ap.add_argument("--summary-out", default="")
+    ap.add_argument("--summarize-launches", default="",
+                    help="(no GPU) print the per-kernel table of an ncu --csv launch list")
     ap.add_argument("--ncu-command", default="", help="the ncu command line recorded in the summary")
     ap.add_argument("--no-batch64", dest="batch64", action="store_false",
                     help="skip the batching configuration: R-MAT scale 24 built on the device, 64 queries to "
@@ -301,6 +303,26 @@ def summarize_ncu(csv_path, out_path, names, trials, command, workload):
         json.dump(out, f, indent=1)
         f.write("\n")
     return out
+
+
+def summarize_launches(csv_path):
+    """Per-kernel launches, summed gpu__time_duration and share of the total, from an
+    ncu --csv launch list (one metric per launch); returns rows sorted by time."""
+    import csv
+    with open(csv_path) as f:
+        lines = [ln for ln in f if ln.startswith('"')]
+    per = {}
+    scale = {"nsecond": 1e-6, "usecond": 1e-3, "msecond": 1.0, "second": 1e3}
+    for r in csv.DictReader(lines):
+        if r.get("Metric Name") != "gpu__time_duration.sum":
+            continue
+        name = r["Kernel Name"].split("(")[0].strip()
+        ms = float(r["Metric Value"].replace(",", "")) * scale.get(r.get("Metric Unit", "nsecond"), 1e-6)
+        e = per.setdefault(name, [0, 0.0])
+        e[0] += 1
+        e[1] += ms
+    total = sum(v[1] for v in per.values()) or 1.0
+    return sorted(((k, v[0], v[1], v[1] / total) for k, v in per.items()), key=lambda x: -x[2])
 
 
 # ------------------------------------------------------------------ wall-time plan
@@ -1156,6 +1178,12 @@ def run_reference(args, world, rank):
 
 def main():
     args = parse_args()
+    if args.summarize_launches:
+        rows = summarize_launches(args.summarize_launches)
+        print("| kernel | launches | total ms | share |\n|---|---|---|---|")
+        for k, n, ms, sh in rows:
+            print(f"| `{k}` | {n} | {ms:.1f} | {100 * sh:.2f}% |")
+        return
     if args.summarize_ncu:
         names = [n for n in args.patterns.split(",") if n]
         s = summarize_ncu(args.summarize_ncu, args.summary_out or TRAFFIC_SUMMARY, names, 1 << args.log2_trials,

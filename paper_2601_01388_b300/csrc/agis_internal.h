@@ -222,7 +222,9 @@ const void *sampler_function(bool dump, bool anchor);
 // launch.cu.  anchor: some staged query uses the anchor draw (selects the instance)
 int launch_sampler(agis_graph *g, LaunchBuffers &lb, int grid, const DumpView *dump,
                    cudaStream_t stream, uint64_t implicit_first, uint64_t implicit_count,
-                   uint64_t *tile_out, bool anchor);
+                   uint32_t implicit_span, uint64_t *tile_out, bool anchor);
+// tiles per work item for an epoch of `tiles` tiles on `grid` CTAs (runtime.cu)
+int span_for(const agis_graph *g, size_t tiles, int grid);
 int add_sampler_node(agis_graph *g, LaunchBuffers &lb, int grid, cudaGraph_t graph,
                      const cudaGraphNode_t *deps, size_t ndeps, cudaGraphNode_t *node, bool anchor);
 int sampler_occupancy(int *blocks_per_sm);

@@ -291,7 +291,7 @@ extern "C" int agis_graph_load_tables(agis_graph *g, const char *path)
     for (auto &kv : g->tables) free_table(kv.second);
     g->tables.clear();
     g->prepped = false;
-    const size_t nv = (size_t)g->nv, nnz = (size_t)g->nnz;
+    const size_t nv = (size_t)g->nv;
     if (!g->nsum) AGIS_CUDA_TRY(cudaMalloc(&g->nsum, sizeof(uint64_t) * std::max<size_t>(nv, 1)));
     if (!g->hits) AGIS_CUDA_TRY(cudaMalloc(&g->hits, sizeof(uint32_t) * std::max<size_t>(nv, 1)));
     PinnedStage stage;

@@ -9,6 +9,11 @@
 
 #include "agis_internal.h"
 
+// Tiles per work item of agis_sample_device's implicit items (at most kMaxSpan).
+#ifndef AGIS_SAMPLE_SPAN
+#define AGIS_SAMPLE_SPAN 1
+#endif
+
 namespace agis {
 
 std::atomic<uint64_t> g_launches{0};
@@ -434,7 +439,7 @@ int run_epoch_direct(agis_graph *g, std::vector<QueryRun *> &runs, const std::ve
     AGIS_CUDA_TRY(cudaMemcpyAsync(lb.d_counter, lb.h_counter, 2 * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
     const int grid = grid_for(g, n);
     if ((rc = ensure_scratch(g, lb, grid)) != AGIS_OK) return rc;
-    rc = launch_sampler(g, lb, grid, nullptr, st, 0, 0, nullptr, any_anchor(runs));
+    rc = launch_sampler(g, lb, grid, nullptr, st, 0, 0, 1, nullptr, any_anchor(runs));
     if (rc != AGIS_OK) return rc;
     AGIS_CUDA_TRY(cudaMemcpyAsync(lb.h_out, lb.d_out, sizeof(uint64_t) * kTileWords * total, cudaMemcpyDeviceToHost, st));
     AGIS_CUDA_TRY(cudaStreamSynchronize(st));
@@ -770,7 +775,7 @@ extern "C" int agis_dump_trials(agis_graph *g, const agis_pattern *p, const agis
     cudaMemcpyAsync(lb.d_counter, lb.h_counter, 2 * sizeof(uint32_t), cudaMemcpyHostToDevice, st);
     const int grid = grid_for(g, ntiles);
     if (rc == AGIS_OK) rc = ensure_scratch(g, lb, grid);
-    if (rc == AGIS_OK) rc = launch_sampler(g, lb, grid, &dv, st, first, count, nullptr, true);
+    if (rc == AGIS_OK) rc = launch_sampler(g, lb, grid, &dv, st, first, count, 1, nullptr, true);
     cudaError_t e = cudaStreamSynchronize(st);
     if (rc == AGIS_OK && e != cudaSuccess) rc = AGIS_ERR_CUDA;
     if (rc == AGIS_OK && emb && cudaMemcpy(emb, dv.emb, sizeof(int32_t) * kMaxK * c, cudaMemcpyDeviceToHost) != cudaSuccess) rc = AGIS_ERR_CUDA;
@@ -800,12 +805,15 @@ extern "C" int agis_sample_device(agis_graph *g, const agis_pattern *p, const ag
     // pageable sources: the runtime stages them before the call returns, so back to
     // back calls never wait for the device (the copies are stream-ordered after the
     // previous launch, which is what keeps the shared device slots safe)
-    const uint32_t counter[2] = {0u, (uint32_t)ntiles};
+    // items of up to AGIS_SAMPLE_SPAN tiles (fewer CTA barriers), smaller while that
+    // would leave CTAs without work; each tile keeps its own sums and slot
+    const int grid = grid_for(g, ntiles);
+    const int span = std::min(AGIS_SAMPLE_SPAN, span_for(g, ntiles, grid));
+    const uint32_t counter[2] = {0u, (uint32_t)((ntiles + span - 1) / span)};
     AGIS_CUDA_TRY(cudaMemcpyAsync(lb.d_queries, &dq, sizeof(DevQuery), cudaMemcpyHostToDevice, st));
     AGIS_CUDA_TRY(cudaMemcpyAsync(lb.d_counter, counter, sizeof(counter), cudaMemcpyHostToDevice, st));
-    const int grid = grid_for(g, ntiles);
     if ((rc = ensure_scratch(g, lb, grid)) != AGIS_OK) return rc;
-    return launch_sampler(g, lb, grid, nullptr, st, first, ntiles * kTile, tile_out,
+    return launch_sampler(g, lb, grid, nullptr, st, first, ntiles * kTile, (uint32_t)span, tile_out,
                           (dq.flags & kFlagAnchor) != 0);
 }
 
@@ -876,7 +884,7 @@ extern "C" int agis_autotune(agis_graph *g, int n, const agis_pattern *const *pa
         cudaMemcpyAsync(lb.d_counter, counter, sizeof(counter), cudaMemcpyHostToDevice, st);
         const int grid = (int)std::min<size_t>((size_t)g->ctx->sm_count * (size_t)c, m);
         cudaEventRecord(e0, st);
-        rc = launch_sampler(g, lb, grid, nullptr, st, 0, 0, nullptr, anchor);
+        rc = launch_sampler(g, lb, grid, nullptr, st, 0, 0, 1, nullptr, anchor);
         cudaEventRecord(e1, st);
         if (rc != AGIS_OK) break;
         if (cudaEventSynchronize(e1) != cudaSuccess) { rc = AGIS_ERR_CUDA; break; }

@@ -118,6 +118,15 @@ __device__ __forceinline__ uint64_t excluded_upto(int64_t pos, uint32_t xmask, i
     return s;
 }
 
+// A load from the graph or its tables, read-only for the whole launch (__ldg), or,
+// with `list`, from a candidate list written earlier in this launch (a coherent load:
+// the read-only path is only defined for data no thread writes during the kernel).
+template <typename T>
+__device__ __forceinline__ T ld_src(const T *p, bool list)
+{
+    return list ? *p : __ldg(p);
+}
+
 // First index j in [0, n) with F(j) > r, where F(j) = P[j] minus the excluded
 // weight at or before j (or F(j) = j + 1 minus the excluded count when P is null).
 // Excluded entries live one per lane (bits of xmask) as a key and a weight; the key
@@ -126,7 +135,7 @@ __device__ __forceinline__ uint64_t excluded_upto(int64_t pos, uint32_t xmask, i
 // the range into 32 parts and one ballot picks the part, so a row of d entries takes
 // ceil(log32 d) rounds of independent loads.
 __device__ int64_t warp_find(const uint64_t *P, int64_t n, uint64_t r, uint32_t xmask, int64_t xkey,
-                             uint64_t xq, const int32_t *ids, int lane)
+                             uint64_t xq, const int32_t *ids, int lane, bool list = false)
 {
     int64_t lo = 0, hi = n;
     while (hi - lo > 32) {
@@ -140,7 +149,7 @@ __device__ int64_t warp_find(const uint64_t *P, int64_t n, uint64_t r, uint32_t 
         }
         bool gt = true;
         if (pos < hi - 1) {
-            const uint64_t f = (P ? __ldg(P + pos) : (uint64_t)(pos + 1)) - ex;
+            const uint64_t f = (P ? ld_src(P + pos, list) : (uint64_t)(pos + 1)) - ex;
             gt = f > r;
         }
         const int f = __ffs(__ballot_sync(kFull, gt)) - 1;
@@ -157,7 +166,7 @@ __device__ int64_t warp_find(const uint64_t *P, int64_t n, uint64_t r, uint32_t 
         ex = excluded_upto(key, xmask, xkey, xq);
     }
     bool gt = true;
-    if (pos < hi) gt = ((P ? __ldg(P + pos) : (uint64_t)(pos + 1)) - ex) > r;
+    if (pos < hi) gt = ((P ? ld_src(P + pos, list) : (uint64_t)(pos + 1)) - ex) > r;
     return lo + (__ffs(__ballot_sync(kFull, gt)) - 1);
 }
 
@@ -223,6 +232,19 @@ __device__ __forceinline__ uint64_t warp_incl_scan(uint64_t v, int lane)
 
 // Per-trial output: X, hit flag and the three sector counts (the model, its streamed
 // part, and the survey's plain count).
+// Paths that few steps take (the per-lane merge, the merge or search filter of rows
+// without a bitmap, the list-free scan of an overflowing step) are compiled out of
+// line with AGIS_OUTLINE_COLD=1, so that the hot loop of this large kernel takes less
+// instruction cache (instruction fetch is its first stall reason).
+#ifndef AGIS_OUTLINE_COLD
+#define AGIS_OUTLINE_COLD 1
+#endif
+#if AGIS_OUTLINE_COLD
+#define AGIS_COLD __noinline__
+#else
+#define AGIS_COLD
+#endif
+
 struct TrialOut {
     double x;
     uint64_t sectors, streamed, survey;
@@ -316,13 +338,6 @@ constexpr int kGroups = AGIS_FILTER_GROUPS;
 #ifndef AGIS_MERGE_RATIO
 #define AGIS_MERGE_RATIO 0
 #endif
-// A hub row (one with a bitmap) is merged by the whole warp instead of probed entry
-// by entry while m <= AGIS_HUB_MERGE_RATIO * n: the merge reads the row once, in
-// coalesced 128-byte windows that often hit L2 (hub rows are the hot ones), where
-// the probes fetch one 32-byte bitmap sector per entry.
-#ifndef AGIS_HUB_MERGE_RATIO
-#define AGIS_HUB_MERGE_RATIO 0
-#endif
 
 // Running weights of out[0, cnt): gathers q for two windows at a time.
 __device__ __forceinline__ uint64_t weigh_list(const int32_t *out, uint32_t cnt, uint64_t *out_pw,
@@ -356,16 +371,16 @@ __device__ __forceinline__ uint64_t weigh_list(const int32_t *out, uint32_t cnt,
 // loads hit L1); survivors go to the lane's own stretch of tmp (at the segment's
 // offset, so at most n entries), then are compacted in order into out.
 template <bool kWeigh>
-__device__ uint32_t filter_lane_merge(const int32_t *L, uint32_t n, const int32_t *R, int64_t m,
-                                      const int32_t *tau_s, int tau_n, int32_t *out, int32_t *tmp,
-                                      uint64_t *out_pw, uint32_t cap, const uint64_t *q, bool approx,
-                                      uint64_t *W, int lane)
+__device__ AGIS_COLD uint32_t filter_lane_merge(const int32_t *L, bool Llist, uint32_t n, const int32_t *R,
+                                                int64_t m, const int32_t *tau_s, int tau_n, int32_t *out,
+                                                int32_t *tmp, uint64_t *out_pw, uint32_t cap, const uint64_t *q,
+                                                bool approx, uint64_t *W, int lane)
 {
     const uint32_t seg = (n + 31) >> 5;
     const uint32_t l0 = min(n, (uint32_t)lane * seg), l1 = min(n, l0 + seg);
     uint32_t c = 0;
     if (l0 < l1 && m > 0) {
-        const int32_t first = __ldg(L + l0);
+        const int32_t first = ld_src(L + l0, Llist);
         int64_t lo = 0, len = m;                  // first j with R[j] >= first
         while (len > 0) {
             const int64_t half = len >> 1;
@@ -378,7 +393,7 @@ __device__ uint32_t filter_lane_merge(const int32_t *L, uint32_t n, const int32_
             for (;;) {
                 if (x < y) {
                     if (++i >= l1) break;
-                    x = __ldg(L + i);
+                    x = ld_src(L + i, Llist);
                 } else if (x > y) {
                     if (++j >= m) break;
                     y = __ldg(R + j);
@@ -387,7 +402,7 @@ __device__ uint32_t filter_lane_merge(const int32_t *L, uint32_t n, const int32_
                     for (int t = 0; t < tau_n; ++t) ok = ok && (x != tau_s[t]);
                     if (ok) tmp[l0 + c++] = x;
                     if (++i >= l1 || ++j >= m) break;
-                    x = __ldg(L + i);
+                    x = ld_src(L + i, Llist);
                     y = __ldg(R + j);
                 }
             }
@@ -408,8 +423,65 @@ __device__ uint32_t filter_lane_merge(const int32_t *L, uint32_t n, const int32_
     return total;
 }
 
+// The filter of filter_list against a row without a bitmap: a warp merge (the row
+// read once in coalesced 32-entry windows, each located among the list window's
+// entries by a shuffle search) or one binary search per list entry, whichever the
+// sizes make cheaper.
 template <bool kWeigh>
-__device__ uint32_t filter_list(const int32_t *L, uint32_t n, const int32_t *R, int64_t m,
+__device__ AGIS_COLD uint32_t filter_merge_search(const int32_t *L, uint32_t n, const int32_t *R, int64_t m,
+                                                  const int32_t *tau_s, int tau_n, int32_t *out, uint64_t *out_pw,
+                                                  uint32_t cap, const uint64_t *q, bool approx, uint64_t *W,
+                                                  int lane)
+{
+    uint32_t cnt = 0;
+    uint64_t carry = 0;
+    int lg = 1;
+    while ((1ll << lg) < m + 1) ++lg;
+    const bool merge = ((int64_t)n + m + 31) / 32 <= (((int64_t)n + 31) / 32) * lg;
+    int64_t rpos = 0;
+    for (uint32_t base = 0; base < n; base += 32) {
+        const uint32_t idx = base + lane;
+        const bool valid = idx < n;
+        const int32_t x = valid ? L[idx] : 0x7fffffff;
+        bool ok = valid;
+        for (int j = 0; j < tau_n; ++j) ok &= (x != tau_s[j]);
+        if (merge) {
+            const int last = (n - base) >= 32 ? 31 : (int)(n - base - 1);
+            const int32_t x_last = __shfl_sync(kFull, x, last);
+            uint32_t found = 0;
+            for (;;) {
+                const bool rvalid = rpos + lane < m;
+                const int32_t rv = rvalid ? __ldg(R + rpos + lane) : 0x7fffffff;
+                // position of rv among the window's entries (lanes 0..last, ascending)
+                int lo = 0, len = last + 1;
+                while (len > 1) {
+                    const int half = len >> 1;
+                    const int32_t xv = __shfl_sync(kFull, x, lo + half);
+                    if (xv <= rv) lo += half;
+                    len -= half;
+                }
+                const int32_t xlo = __shfl_sync(kFull, x, lo);
+                uint32_t bit = (rvalid && xlo == rv) ? (1u << lo) : 0u;
+                for (int o = 16; o > 0; o >>= 1) bit |= __shfl_xor_sync(kFull, bit, o);
+                found |= bit;
+                const int c = __popc(__ballot_sync(kFull, rvalid && rv <= x_last));
+                rpos += c;
+                if (c < 32) break;
+            }
+            ok = ok && ((found >> lane) & 1u);
+        } else if (ok) {
+            ok = row_find(R, m, x) >= 0;
+        }
+        const uint64_t w = (kWeigh && ok) ? (approx ? __ldg(q + x) : 1u) : 0u;
+        emit_window<kWeigh>(ok, x, w, out, out_pw, cap, cnt, carry, lane);
+        if (cnt > cap) return cnt;
+    }
+    if (kWeigh) *W = carry;
+    return cnt;
+}
+
+template <bool kWeigh>
+__device__ uint32_t filter_list(const int32_t *L, bool Llist, uint32_t n, const int32_t *R, int64_t m,
                                 const uint32_t *Rbits, const int32_t *tau_s, int tau_n, int32_t *out,
                                 uint64_t *out_pw, uint32_t cap, const uint64_t *q, bool approx, uint64_t *W,
                                 int lane)
@@ -419,9 +491,9 @@ __device__ uint32_t filter_list(const int32_t *L, uint32_t n, const int32_t *R, 
     // tmp: the id staging of the per-lane merge lives in the (not yet written)
     // running-weight array of out's list, room for 2 * cap ids
     if (R && n >= 256 && m >= 256 && n <= 2 * cap && (!Rbits || m < (int64_t)AGIS_MERGE_RATIO * n))
-        return filter_lane_merge<kWeigh>(L, n, R, m, tau_s, tau_n, out, reinterpret_cast<int32_t *>(out_pw),
+        return filter_lane_merge<kWeigh>(L, Llist, n, R, m, tau_s, tau_n, out, reinterpret_cast<int32_t *>(out_pw),
                                          out_pw, cap, q, approx, W, lane);
-    if (!R || (Rbits && !((int64_t)m <= (int64_t)AGIS_HUB_MERGE_RATIO * (int64_t)n))) {
+    if (Rbits || !R) {
         // Survivor ids first: 16-byte loads of four consecutive entries per lane,
         // kGroups groups of 128 entries per iteration, so 4 * kGroups bitmap probes
         // per lane are in flight together; the survivors' weights are gathered afterwards in
@@ -436,7 +508,7 @@ __device__ uint32_t filter_list(const int32_t *L, uint32_t n, const int32_t *R, 
 #pragma unroll
             for (int gi = 0; gi < kGroups; ++gi) {
                 const uint32_t k = base + 128 * gi + 4 * lane;
-                v[gi] = k < total ? __ldg(reinterpret_cast<const int4 *>(La + k)) : make_int4(0, 0, 0, 0);
+                v[gi] = k < total ? ld_src(reinterpret_cast<const int4 *>(La + k), Llist) : make_int4(0, 0, 0, 0);
             }
             unsigned okm[kGroups];
 #pragma unroll
@@ -499,49 +571,82 @@ __device__ uint32_t filter_list(const int32_t *L, uint32_t n, const int32_t *R, 
         }
         return cnt;
     }
-    int lg = 1;
-    while ((1ll << lg) < m + 1) ++lg;
-    const bool merge = ((int64_t)n + m + 31) / 32 <= (((int64_t)n + 31) / 32) * lg;
-    int64_t rpos = 0;
-    for (uint32_t base = 0; base < n; base += 32) {
-        const uint32_t idx = base + lane;
-        const bool valid = idx < n;
-        const int32_t x = valid ? L[idx] : 0x7fffffff;
-        bool ok = valid;
-        for (int j = 0; j < tau_n; ++j) ok &= (x != tau_s[j]);
-        if (merge) {
-            const int last = (n - base) >= 32 ? 31 : (int)(n - base - 1);
-            const int32_t x_last = __shfl_sync(kFull, x, last);
-            uint32_t found = 0;
-            for (;;) {
-                const bool rvalid = rpos + lane < m;
-                const int32_t rv = rvalid ? __ldg(R + rpos + lane) : 0x7fffffff;
-                // position of rv among the window's entries (lanes 0..last, ascending)
-                int lo = 0, len = last + 1;
-                while (len > 1) {
-                    const int half = len >> 1;
-                    const int32_t xv = __shfl_sync(kFull, x, lo + half);
-                    if (xv <= rv) lo += half;
-                    len -= half;
-                }
-                const int32_t xlo = __shfl_sync(kFull, x, lo);
-                uint32_t bit = (rvalid && xlo == rv) ? (1u << lo) : 0u;
-                for (int o = 16; o > 0; o >>= 1) bit |= __shfl_xor_sync(kFull, bit, o);
-                found |= bit;
-                const int c = __popc(__ballot_sync(kFull, rvalid && rv <= x_last));
-                rpos += c;
-                if (c < 32) break;
+    return filter_merge_search<kWeigh>(L, n, R, m, tau_s, tau_n, out, out_pw, cap, q, approx, W, lane);
+}
+
+// The list-free scan of a several-backward step whose survivors overflow the
+// warp's list: the anchor row is filtered window by window, the running weight of
+// every 32nd part of the windows is kept one per lane, and after the draw only the
+// part holding r is filtered again.  Returns W (0: empty S or zero weight) and sets
+// the drawn vertex v, its weight qv and the survivor count nsurv.
+__device__ AGIS_COLD uint64_t list_free_draw(const GraphView &g, const DevStep &S, const int32_t *tau_s, int i,
+                                             int64_t a_start, int64_t da, const RowRef *rows, int n_filter,
+                                             uint64_t t, uint64_t seed, int lane, int32_t &v, uint64_t &qv,
+                                             uint64_t &nsurv)
+{
+    const int64_t nwin = (da + 31) >> 5;
+    const int64_t bsz = (nwin + 31) >> 5;              // windows per bucket
+    uint64_t running = 0, bucket_end = 0;
+    nsurv = 0;
+    // last window kept in registers (most rows need a single window)
+    uint64_t last_before = 0, last_incl = 0, last_w = 0;
+    int32_t last_x = -1;
+    constexpr int U = 4;       // windows whose loads are in flight together
+    for (int64_t w0 = 0; w0 < nwin; w0 += U) {
+        bool okv[U];
+        int32_t xv[U];
+        uint64_t wtv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            wtv[u] = window_weight(g, S, tau_s, i, a_start, da, (w0 + u) * 32 + lane, rows, n_filter, okv[u], xv[u]);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t w = w0 + u;
+            if (w >= nwin) break;
+            nsurv += __popc(__ballot_sync(kFull, okv[u]));
+            const uint64_t incl = warp_incl_scan(wtv[u], lane);
+            const uint64_t wtot = __shfl_sync(kFull, incl, 31);
+            last_before = running;
+            last_incl = incl;
+            last_w = wtv[u];
+            last_x = xv[u];
+            running += wtot;
+            if ((w + 1) % bsz == 0 || w == nwin - 1) {
+                if (lane == (int)(w / bsz)) bucket_end = running;
             }
-            ok = ok && ((found >> lane) & 1u);
-        } else if (ok) {
-            ok = row_find(R, m, x) >= 0;
         }
-        const uint64_t w = (kWeigh && ok) ? (approx ? __ldg(q + x) : 1u) : 0u;
-        emit_window<kWeigh>(ok, x, w, out, out_pw, cap, cnt, carry, lane);
-        if (cnt > cap) return cnt;
     }
-    if (kWeigh) *W = carry;
-    return cnt;
+    const uint64_t W = running;
+    if (W == 0) return 0;
+    const uint64_t r = draw_below(W, t, (uint64_t)(i + 1), kStreamTrial, seed);
+    if (r >= last_before) {
+        const bool hit = last_w > 0 && last_before + last_incl > r;
+        const int src = __ffs(__ballot_sync(kFull, hit)) - 1;
+        v = __shfl_sync(kFull, last_x, src);
+        qv = __shfl_sync(kFull, last_w, src);
+    } else {
+        const int64_t nbuck = (nwin + bsz - 1) / bsz;
+        const int b = __ffs(__ballot_sync(kFull, lane < nbuck && bucket_end > r)) - 1;
+        const uint64_t prev = __shfl_sync(kFull, bucket_end, b > 0 ? b - 1 : 0);
+        uint64_t run2 = b > 0 ? prev : 0;
+        const int64_t w_end = (b + 1) * bsz < nwin ? (b + 1) * bsz : nwin;
+        for (int64_t w = (int64_t)b * bsz; w < w_end; ++w) {
+            bool ok;
+            int32_t x;
+            const uint64_t wt = window_weight(g, S, tau_s, i, a_start, da, w * 32 + lane, rows, n_filter, ok, x);
+            const uint64_t incl = warp_incl_scan(wt, lane);
+            const uint64_t wtot = __shfl_sync(kFull, incl, 31);
+            if (run2 + wtot > r) {
+                const bool hit = wt > 0 && run2 + incl > r;
+                const int src = __ffs(__ballot_sync(kFull, hit)) - 1;
+                v = __shfl_sync(kFull, x, src);
+                qv = __shfl_sync(kFull, wt, src);
+                break;
+            }
+            run2 += wtot;
+        }
+    }
+    return W;
 }
 
 // Alg. 3 for trial t of query Q; all 32 lanes call it together.  tau_s is the
@@ -762,10 +867,10 @@ __device__ TrialOut run_trial(const GraphView &g, const DevQuery &Q, uint64_t t,
                     // so such a query keeps counts in the weighted instance.
                     const bool last = pss == passes - 1;
                     if (last && weigh) {
-                        n = filter_list<true>(src, n, R, m, Rb, tau_s, pss == 0 ? tau_n : 0, ws.xs[nxt],
+                        n = filter_list<true>(src, reuse || pss > 0, n, R, m, Rb, tau_s, pss == 0 ? tau_n : 0, ws.xs[nxt],
                                               ws.pw[nxt], ws.cap, S.q, S.approx != 0, &Wl, lane);
                     } else {
-                        n = filter_list<false>(src, n, R, m, Rb, tau_s, pss == 0 ? tau_n : 0, ws.xs[nxt],
+                        n = filter_list<false>(src, reuse || pss > 0, n, R, m, Rb, tau_s, pss == 0 ? tau_n : 0, ws.xs[nxt],
                                                ws.pw[nxt], ws.cap, S.q, S.approx != 0, nullptr, lane);
                         if (!last) {
                             src = ws.xs[nxt];
@@ -787,7 +892,7 @@ __device__ TrialOut run_trial(const GraphView &g, const DevQuery &Q, uint64_t t,
                 if (W == 0) { STORE_SECTORS(out); return out; }
                 const uint64_t r = draw_below(W, t, (uint64_t)(i + 1), kStreamTrial, Q.seed);
                 // equal weights: the r-th survivor (r < W = n)
-                const int64_t j = S.approx ? warp_find(ws.pw[cur], n, r, 0u, 0, 0, nullptr, lane) : (int64_t)r;
+                const int64_t j = S.approx ? warp_find(ws.pw[cur], n, r, 0u, 0, 0, nullptr, lane, true) : (int64_t)r;
                 v = ws.xs[cur][j];
                 qv = S.approx ? ws.pw[cur][j] - (j > 0 ? ws.pw[cur][j - 1] : 0) : 1u;
                 if (anch) {
@@ -802,71 +907,11 @@ __device__ TrialOut run_trial(const GraphView &g, const DevQuery &Q, uint64_t t,
                 continue;
             }
             cur = -1;
-            const int64_t nwin = (da + 31) >> 5;
-            const int64_t bsz = (nwin + 31) >> 5;              // windows per bucket
-            uint64_t running = 0, bucket_end = 0, nsurv = 0;
-            // last window kept in registers (most rows need a single window)
-            uint64_t last_before = 0, last_incl = 0, last_w = 0;
-            int32_t last_x = -1;
-            constexpr int U = 4;       // windows whose loads are in flight together
-            for (int64_t w0 = 0; w0 < nwin; w0 += U) {
-                bool okv[U];
-                int32_t xv[U];
-                uint64_t wtv[U];
-#pragma unroll
-                for (int u = 0; u < U; ++u)
-                    wtv[u] = window_weight(g, S, tau_s, i, a_start, da, (w0 + u) * 32 + lane, rows,
-                                           n_filter, okv[u], xv[u]);
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const int64_t w = w0 + u;
-                    if (w >= nwin) break;
-                    nsurv += __popc(__ballot_sync(kFull, okv[u]));
-                    const uint64_t incl = warp_incl_scan(wtv[u], lane);
-                    const uint64_t wtot = __shfl_sync(kFull, incl, 31);
-                    last_before = running;
-                    last_incl = incl;
-                    last_w = wtv[u];
-                    last_x = xv[u];
-                    running += wtot;
-                    if ((w + 1) % bsz == 0 || w == nwin - 1) {
-                        if (lane == (int)(w / bsz)) bucket_end = running;
-                    }
-                }
-            }
+            uint64_t nsurv = 0;
+            W = list_free_draw(g, S, tau_s, i, a_start, da, rows, n_filter, t, Q.seed, lane, v, qv, nsurv);
             if (S.approx && S.nb > 1 && !anch) sec += nsurv;
             if (S.dapprox && S.nb > 1 && !anch) ADD_SV(nsurv);
-            W = running;
             if (W == 0) { STORE_SECTORS(out); return out; }
-            const uint64_t r = draw_below(W, t, (uint64_t)(i + 1), kStreamTrial, Q.seed);
-            if (r >= last_before) {
-                const bool hit = last_w > 0 && last_before + last_incl > r;
-                const int src = __ffs(__ballot_sync(kFull, hit)) - 1;
-                v = __shfl_sync(kFull, last_x, src);
-                qv = __shfl_sync(kFull, last_w, src);
-            } else {
-                const int64_t nbuck = (nwin + bsz - 1) / bsz;
-                const int b = __ffs(__ballot_sync(kFull, lane < nbuck && bucket_end > r)) - 1;
-                const uint64_t prev = __shfl_sync(kFull, bucket_end, b > 0 ? b - 1 : 0);
-                uint64_t run2 = b > 0 ? prev : 0;
-                const int64_t w_end = (b + 1) * bsz < nwin ? (b + 1) * bsz : nwin;
-                for (int64_t w = (int64_t)b * bsz; w < w_end; ++w) {
-                    bool ok;
-                    int32_t x;
-                    const uint64_t wt = window_weight(g, S, tau_s, i, a_start, da, w * 32 + lane,
-                                                      rows, n_filter, ok, x);
-                    const uint64_t incl = warp_incl_scan(wt, lane);
-                    const uint64_t wtot = __shfl_sync(kFull, incl, 31);
-                    if (run2 + wtot > r) {
-                        const bool hit = wt > 0 && run2 + incl > r;
-                        const int src = __ffs(__ballot_sync(kFull, hit)) - 1;
-                        v = __shfl_sync(kFull, x, src);
-                        qv = __shfl_sync(kFull, wt, src);
-                        break;
-                    }
-                    run2 += wtot;
-                }
-            }
         }
         if (i > 0 && !direct) {
             STEP_T1(4)
@@ -887,8 +932,9 @@ __device__ TrialOut run_trial(const GraphView &g, const DevQuery &Q, uint64_t t,
 #undef ADD_SV
 
 // Work items come from `items`, or, when it is null, are implicit: item j covers
-// trials [implicit_first + kTile j, ...) of query 0 up to implicit_count trials and
-// writes slot j.  n_items_ptr[0] holds the number of items.
+// implicit_span tiles, trials [implicit_first + kTile implicit_span j, ...) of query 0
+// up to implicit_count trials, and writes slots implicit_span j, ...  n_items_ptr[0]
+// holds the number of items.
 // kAnchor: the instance that can run anchor-draw queries (the other one compiles
 // that code away; both give the same results for queries without the flag)
 template <bool kDump, bool kAnchor>
@@ -897,7 +943,8 @@ __global__ void __launch_bounds__(kBlock, AGIS_MIN_BLOCKS) sample_kernel(GraphVi
                                                         const uint32_t *__restrict__ n_items_ptr,
                                                         uint32_t *counter, uint64_t *tile_out,
                                                         DumpView dump, uint64_t implicit_first,
-                                                        uint64_t implicit_count, char *scratch,
+                                                        uint64_t implicit_count, uint32_t implicit_span,
+                                                        char *scratch,
                                                         uint32_t scratch_cap)
 {
     __shared__ DevQuery sq;
@@ -939,12 +986,13 @@ __global__ void __launch_bounds__(kBlock, AGIS_MIN_BLOCKS) sample_kernel(GraphVi
                 if (items) {
                     w = items[id];
                 } else {
-                    const uint64_t done = (uint64_t)id * kTile;
+                    const uint64_t per = (uint64_t)kTile * implicit_span;
+                    const uint64_t done = (uint64_t)id * per;
                     const uint64_t left = implicit_count - done;
                     w.query = 0;
-                    w.count = (uint32_t)(left < (uint64_t)kTile ? left : (uint64_t)kTile);
+                    w.count = (uint32_t)(left < per ? left : per);
                     w.first = implicit_first + done;
-                    w.slot = id;
+                    w.slot = (uint64_t)id * implicit_span;
                 }
                 s_it = w;
                 s_reload = (int)w.query != s_query;

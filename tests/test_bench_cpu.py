@@ -73,3 +73,17 @@ def test_ncu_summary_round_trip(tmp_path):
     assert s["per_pattern"]["5-cycle"]["dram_gbs"] == 2.5e9 / 1e6
     got = bench.profile_traffic(str(out))
     assert got == {"4-clique": 5e9 / (1 << 20), "5-cycle": 2.5e9 / (1 << 20)}
+
+
+def test_launch_list_summary(tmp_path):
+    sys.path.insert(0, ROOT)
+    import bench
+    hdr = '"ID","Kernel Name","Metric Name","Metric Unit","Metric Value"\n'
+    rows = ['"0","void agis::sample_kernel<0, 0>(GraphView)","gpu__time_duration.sum","msecond","3"\n',
+            '"1","k_scan_apply(const unsigned long *)","gpu__time_duration.sum","usecond","500"\n',
+            '"2","void agis::sample_kernel<0, 0>(GraphView)","gpu__time_duration.sum","msecond","0.5"\n']
+    p = tmp_path / "l.csv"
+    p.write_text(hdr + "".join(rows))
+    got = bench.summarize_launches(str(p))
+    assert [(k, n) for k, n, _, _ in got] == [("void agis::sample_kernel<0, 0>", 2), ("k_scan_apply", 1)]
+    assert abs(got[0][2] - 3.5) < 1e-9 and abs(got[0][3] - 0.875) < 1e-9
