@@ -50,6 +50,9 @@ sys.path.insert(0, ROOT)
 METRIC = "samples/s & time-to-±1% err (95% CI), batched/served vs plain, 1 B300"
 PATTERN_NAMES = ["4-clique", "5-cycle", "house", "5-clique"]
 CMIN = 2.0 ** -10
+# Alg. 1 checkpoint spacing (and first checkpoint) of the optional legs that run
+# queries to +-1% (the time-to-+-1% legs take theirs from --tte-chunk-log2)
+CHECKPOINT = 1 << 12
 
 
 def parse_args(argv=None):
@@ -305,19 +308,27 @@ def summarize_ncu(csv_path, out_path, names, trials, command, workload):
     return out
 
 
-def summarize_launches(csv_path):
-    """Per-kernel launches, summed gpu__time_duration and share of the total, from an
-    ncu --csv launch list (one metric per launch); returns rows sorted by time."""
+def summarize_launches(csv_path, by="kernel"):
+    """Launches, summed gpu__time_duration and share of the total from an ncu --csv
+    launch list (one metric per launch), per kernel or (by="nvtx", for a capture
+    taken with --nvtx) per innermost NVTX range of this library ("agis:...", else
+    "(none)"); returns rows sorted by time."""
     import csv
+    import re
     with open(csv_path) as f:
         lines = [ln for ln in f if ln.startswith('"')]
     per = {}
-    scale = {"nsecond": 1e-6, "usecond": 1e-3, "msecond": 1.0, "second": 1e3}
+    scale = {"ns": 1e-6, "nsecond": 1e-6, "usecond": 1e-3, "us": 1e-3, "msecond": 1.0, "ms": 1.0, "second": 1e3}
     for r in csv.DictReader(lines):
         if r.get("Metric Name") != "gpu__time_duration.sum":
             continue
-        name = r["Kernel Name"].split("(")[0].strip()
-        ms = float(r["Metric Value"].replace(",", "")) * scale.get(r.get("Metric Unit", "nsecond"), 1e-6)
+        if by == "nvtx":
+            stack = next((v for k, v in r.items() if k and "Push/Pop" in k), "") or ""
+            ranges = re.findall(r"(agis:[a-z_.]+)", stack)
+            name = ranges[-1] if ranges else "(none)"
+        else:
+            name = r["Kernel Name"].split("(")[0].strip()
+        ms = float(r["Metric Value"].replace(",", "")) * scale.get(r.get("Metric Unit", "ns"), 1e-6)
         e = per.setdefault(name, [0, 0.0])
         e[0] += 1
         e[1] += ms
@@ -476,7 +487,7 @@ def _serve_queries(agis, rng, n, seed_base):
     for i in range(n):
         k, e = I.random_connected_pattern(rng, 3, 8, 0.3)
         o = agis.default_opts(mode=0, seed=seed_base + i, eps=float(rng.uniform(0.01, 0.05)), delta=0.05,
-                              chunk_trials=1 << 16, min_trials=1 << 16, max_trials=1 << 24)
+                              chunk_trials=CHECKPOINT, min_trials=CHECKPOINT, max_trials=1 << 24)
         qs.append((agis.Pattern(k, e), o))
     return qs
 
@@ -659,8 +670,8 @@ def large_graph(agis, ctx, scale):
         p = agis.Pattern(*I.PATTERNS[name])
         for mode, label, cap in ((0, "f_approx (D^pi)", 1 << 30), (2, "f_uniform", 1 << 28)):
             g.drop_tables()
-            o = agis.default_opts(mode=mode, seed=7, eps=0.01, delta=0.05, chunk_trials=1 << 16,
-                                  min_trials=1 << 16, max_trials=cap)
+            o = agis.default_opts(mode=mode, seed=7, eps=0.01, delta=0.05, chunk_trials=CHECKPOINT,
+                                  min_trials=CHECKPOINT, max_trials=cap)
             t1 = time.perf_counter()
             agis.prepare(g, p, o)
             t_tab = time.perf_counter() - t1
@@ -697,7 +708,7 @@ def ablation(agis, g, cap_log2=28):
     Runs stop at 2^cap_log2 trials; an unconverged run reports the trials it would
     need, trials * (eps_hat / eps)^2, since the half-width shrinks as 1/sqrt(n)."""
     from paper_2601_01388_b300 import inputs as I
-    acc = dict(eps=0.01, delta=0.05, chunk_trials=1 << 16, min_trials=1 << 16, max_trials=1 << cap_log2)
+    acc = dict(eps=0.01, delta=0.05, chunk_trials=CHECKPOINT, min_trials=CHECKPOINT, max_trials=1 << cap_log2)
 
     def run(p, o):
         g.drop_tables()
@@ -741,8 +752,8 @@ def concentration_run(agis, g, cap_log2=28):
         ps = [agis.Pattern(*p) for p in pats]
         vecs = []
         for rep in range(2):
-            opts = [agis.default_opts(eps=0.01, delta=0.05, seed=1000 * (rep + 1) + i, chunk_trials=1 << 16,
-                                      min_trials=1 << 16, max_trials=1 << cap_log2) for i in range(len(ps))]
+            opts = [agis.default_opts(eps=0.01, delta=0.05, seed=1000 * (rep + 1) + i, chunk_trials=CHECKPOINT,
+                                      min_trials=CHECKPOINT, max_trials=1 << cap_log2) for i in range(len(ps))]
             g.drop_tables()
             t0 = time.perf_counter()
             rs = agis.estimate_batch(g, ps, opts)
@@ -777,8 +788,8 @@ def cliques_oriented(agis, g, cap_log2=30):
     for name in ("4-clique", "5-clique", "6-clique"):
         p = agis.Pattern(*I.PATTERNS[name])
         for label, graph, anchor in (("undirected", g, 0), ("oriented", o, 0), ("oriented+anchor", o, 1)):
-            opts = agis.default_opts(mode=0, seed=53, anchor=anchor, eps=0.01, delta=0.05, chunk_trials=1 << 16,
-                                     min_trials=1 << 16, max_trials=1 << cap_log2)
+            opts = agis.default_opts(mode=0, seed=53, anchor=anchor, eps=0.01, delta=0.05, chunk_trials=CHECKPOINT,
+                                     min_trials=CHECKPOINT, max_trials=1 << cap_log2)
             graph.drop_tables()
             t0 = time.perf_counter()
             agis.prepare(graph, p, opts)
@@ -804,8 +815,8 @@ def anchor_vs_exact(agis, g, names, cap_log2=30):
     for name in names:
         p = agis.Pattern(*I.PATTERNS[name])
         for anchor in (0, 1):
-            o = agis.default_opts(mode=0, seed=61, anchor=anchor, eps=0.01, delta=0.05, chunk_trials=1 << 16,
-                                  min_trials=1 << 16, max_trials=1 << cap_log2)
+            o = agis.default_opts(mode=0, seed=61, anchor=anchor, eps=0.01, delta=0.05, chunk_trials=CHECKPOINT,
+                                  min_trials=CHECKPOINT, max_trials=1 << cap_log2)
             g.drop_tables()
             t0 = time.perf_counter()
             agis.prepare(g, p, o)
@@ -1179,10 +1190,12 @@ def run_reference(args, world, rank):
 def main():
     args = parse_args()
     if args.summarize_launches:
-        rows = summarize_launches(args.summarize_launches)
-        print("| kernel | launches | total ms | share |\n|---|---|---|---|")
-        for k, n, ms, sh in rows:
-            print(f"| `{k}` | {n} | {ms:.1f} | {100 * sh:.2f}% |")
+        for by in ("kernel", "nvtx"):
+            rows = summarize_launches(args.summarize_launches, by)
+            print(f"| {'kernel' if by == 'kernel' else 'NVTX range'} | launches | total ms | share |\n|---|---|---|---|")
+            for k, n, ms, sh in rows:
+                print(f"| `{k}` | {n} | {ms:.1f} | {100 * sh:.2f}% |")
+            print()
         return
     if args.summarize_ncu:
         names = [n for n in args.patterns.split(",") if n]

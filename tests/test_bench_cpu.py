@@ -87,3 +87,12 @@ def test_launch_list_summary(tmp_path):
     got = bench.summarize_launches(str(p))
     assert [(k, n) for k, n, _, _ in got] == [("void agis::sample_kernel<0, 0>", 2), ("k_scan_apply", 1)]
     assert abs(got[0][2] - 3.5) < 1e-9 and abs(got[0][3] - 0.875) < 1e-9
+    nv = tmp_path / "n.csv"
+    nv.write_text('"ID","thread Domain:Push/Pop_Range:PL_Type","Kernel Name","Metric Name","Metric Unit",'
+                  '"Metric Value"\n'
+                  '"0","1 ""<default domain>:agis:load:none"" ","k1(int)","gpu__time_duration.sum","ns","2000000"\n'
+                  '"1","1 ""<default domain>:agis:epoch:none"" ","k2(int)","gpu__time_duration.sum","ns","6000000"\n'
+                  '"2","","k3(int)","gpu__time_duration.sum","ns","2000000"\n')
+    got = bench.summarize_launches(str(nv), by="nvtx")
+    assert [(k, n, round(ms, 6)) for k, n, ms, _ in got] == [("agis:epoch", 1, 6.0), ("agis:load", 1, 2.0),
+                                                            ("(none)", 1, 2.0)]
