@@ -91,6 +91,14 @@ struct DumpView {
     uint64_t first;
 };
 
+// Per-trial outputs of a scatter epoch (see scatter_kernel), indexed by tile slot *
+// kTile + trial within the tile.
+struct ScatterView {
+    double *x;
+    uint8_t *hit;
+    uint64_t *sec;              // 3 words per trial: sectors, streamed, survey
+};
+
 struct GraphView {
     const int64_t *off;
     const int32_t *cols;
@@ -125,6 +133,11 @@ struct LaunchBuffers {
     uint64_t *d_out = nullptr;  // kTileWords words per tile slot
     size_t cap_out = 0;
     uint32_t *d_counter = nullptr; // [0] work counter, [1] number of items
+    // per-trial outputs of scatter epochs (trials of up to cap_scatter)
+    double *d_sx = nullptr;
+    uint8_t *d_shit = nullptr;
+    uint64_t *d_ssec = nullptr;
+    size_t cap_scatter = 0;
     void *d_scratch = nullptr;     // per-warp candidate lists of the sampler
     bool scratch_borrowed = false; // d_scratch belongs to another LaunchBuffers (not freed here)
     size_t scratch_bytes = 0;
@@ -145,6 +158,14 @@ struct LaunchBuffers {
     uint64_t generation = 0;       // bumps when device buffers move (graph must be rebuilt)
     uint64_t graph_generation = ~0ull;
     bool graph_anchor = false;  // the cached graph's kernel node is the anchor-capable instance
+    // the captured scatter epoch: H2D, scatter kernel, tile reduction, D2H
+    cudaGraph_t sgraph = nullptr;
+    cudaGraphExec_t sexec = nullptr;
+    cudaGraphNode_t s_h2d_q = nullptr, s_h2d_i = nullptr, s_h2d_c = nullptr, s_kernel = nullptr, s_reduce = nullptr,
+                    s_d2h = nullptr;
+    int sgraph_grid = 0;
+    uint64_t sgraph_generation = ~0ull;
+    bool sgraph_anchor = false;
 };
 
 }  // namespace agis
@@ -228,6 +249,18 @@ int span_for(const agis_graph *g, size_t tiles, int grid);
 int add_sampler_node(agis_graph *g, LaunchBuffers &lb, int grid, cudaGraph_t graph,
                      const cudaGraphNode_t *deps, size_t ndeps, cudaGraphNode_t *node, bool anchor);
 int sampler_occupancy(int *blocks_per_sm);
+// the scatter kernel instance and the tile reduction of scatter epochs (sample.cu)
+const void *scatter_function(bool anchor);
+const void *tile_reduce_function();
+// launch.cu: a scatter epoch over lb's staged single-tile items (n of them)
+int launch_scatter(agis_graph *g, LaunchBuffers &lb, int grid, size_t n, cudaStream_t stream, bool anchor);
+int add_scatter_nodes(agis_graph *g, LaunchBuffers &lb, int grid, size_t n, cudaGraph_t graph,
+                      const cudaGraphNode_t *deps, size_t ndeps, cudaGraphNode_t *kernel, cudaGraphNode_t *reduce,
+                      bool anchor);
+int set_reduce_node_items(LaunchBuffers &lb, cudaGraphExec_t exec, cudaGraphNode_t node, size_t n);
+// an epoch of `tiles` tiles on a grid of `grid` CTAs runs in scatter mode (runtime.cu)
+bool use_scatter(size_t tiles, int grid);
+int ensure_scatter(LaunchBuffers &lb, size_t tiles);
 
 // runtime.cu
 int make_dev_query(agis_graph *g, const agis_pattern *p, const agis_opts *o, DevQuery *dq,

@@ -686,7 +686,9 @@ __device__ __forceinline__ uint64_t closing_sectors(const GraphView &g, const De
 #define ADD_ST(v) do { if (lane == 0) wsec[0] += (v); } while (0)
 #define ADD_SV(v) do { if (lane == 0) wsec[1] += (v); } while (0)
 
-template <bool kAnchor>
+// kStagedTop: the first two levels of the step-1 search come from the CTA's staged
+// splitters `top` (the main kernel); without them the search reads the prefix only.
+template <bool kAnchor, bool kStagedTop = true>
 __device__ TrialOut run_trial(const GraphView &g, const DevQuery &Q, uint64_t t, int32_t *tau_s,
                               const WarpSets &ws, const uint64_t *top, uint64_t *wsec, RowRef *rows, int lane)
 {
@@ -744,7 +746,8 @@ __device__ TrialOut run_trial(const GraphView &g, const DevQuery &Q, uint64_t t,
             if (W == 0) { STORE_SECTORS(out); return out; }
             const uint64_t r = draw_below(W, t, 1, kStreamTrial, Q.seed);
             const uint64_t *P = S.approx ? S.pref : (const uint64_t *)(g.off + 1);
-            v = (int32_t)warp_find_top(P, g.nv, r, top, lane);
+            v = kStagedTop ? (int32_t)warp_find_top(P, g.nv, r, top, lane)
+                           : (int32_t)warp_find(P, g.nv, r, 0u, 0, 0, nullptr, lane);
             qv = S.approx ? __ldg(S.q + v) : (uint64_t)(__ldg(g.off + v + 1) - __ldg(g.off + v));
             cur = -1;
             STEP_T1(0)
@@ -931,6 +934,32 @@ __device__ TrialOut run_trial(const GraphView &g, const DevQuery &Q, uint64_t t,
 #undef ADD_ST
 #undef ADD_SV
 
+// The fixed-order FP64 reduction of one tile's outputs xs[0, kTile) (zeros past its
+// trials): per thread strided partial sums of x and x^2, then a tree over the
+// threads; the sums end in red[0] and red2[0].  Both the main kernel and the tile
+// reduction of scatter epochs use it, so a tile's sums never depend on the mode.
+__device__ __forceinline__ void tile_fp64_sums(const double *xs, double *red, double *red2)
+{
+    {
+        double s = 0.0, s2 = 0.0;
+        for (int j = threadIdx.x; j < kTile; j += kBlock) {
+            const double x = xs[j];
+            s += x;
+            s2 += x * x;
+        }
+        red[threadIdx.x] = s;
+        red2[threadIdx.x] = s2;
+    }
+    __syncthreads();
+    for (int w = kBlock / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            red[threadIdx.x] += red[threadIdx.x + w];
+            red2[threadIdx.x] += red2[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+}
+
 // Work items come from `items`, or, when it is null, are implicit: item j covers
 // implicit_span tiles, trials [implicit_first + kTile implicit_span j, ...) of query 0
 // up to implicit_count trials, and writes slots implicit_span j, ...  n_items_ptr[0]
@@ -1053,24 +1082,7 @@ __global__ void __launch_bounds__(kBlock, AGIS_MIN_BLOCKS) sample_kernel(GraphVi
         __syncthreads();
         // fixed-order reduction of each tile: strided partial sums, then a tree
         for (int tl = 0; tl < ntile; ++tl) {
-            {
-                double s = 0.0, s2 = 0.0;
-                for (int j = threadIdx.x; j < kTile; j += kBlock) {
-                    const double x = xs[tl * kTile + j];
-                    s += x;
-                    s2 += x * x;
-                }
-                red[threadIdx.x] = s;
-                red2[threadIdx.x] = s2;
-            }
-            __syncthreads();
-            for (int w = kBlock / 2; w > 0; w >>= 1) {
-                if (threadIdx.x < w) {
-                    red[threadIdx.x] += red[threadIdx.x + w];
-                    red2[threadIdx.x] += red2[threadIdx.x + w];
-                }
-                __syncthreads();
-            }
+            tile_fp64_sums(xs + tl * kTile, red, red2);
             if (threadIdx.x == 0) {
                 uint64_t *o = tile_out + kTileWords * ((uint64_t)it.slot + tl);
                 o[0] = s_hits[tl];
@@ -1085,7 +1097,123 @@ __global__ void __launch_bounds__(kBlock, AGIS_MIN_BLOCKS) sample_kernel(GraphVi
     }
 }
 
+// Scatter epochs (epochs of few tiles, e.g. a query's first Alg. 1 checkpoints): in
+// the main kernel one CTA runs a whole tile, 32 trials per warp in sequence, so such
+// an epoch takes as long as 32 trials back to back on an almost idle GPU.  Here every
+// warp of a full grid pulls single trials from the device counter (trial c of the
+// epoch is trial c mod kTile of item c / kTile; items are single tiles) and writes
+// its output to per-trial buffers; tile_reduce_kernel then forms each tile's sums
+// with the main kernel's fixed-order reduction, so the results are the same bits.
+template <bool kAnchor>
+__global__ void __launch_bounds__(kBlock, AGIS_MIN_BLOCKS) scatter_kernel(GraphView g, const DevQuery *__restrict__ queries,
+                                                         const WorkItem *__restrict__ items,
+                                                         const uint32_t *__restrict__ n_items_ptr,
+                                                         uint32_t *counter, ScatterView sv, char *scratch,
+                                                         uint32_t scratch_cap)
+{
+    __shared__ DevQuery wq[kWarps];          // the warp's current query
+    __shared__ int s_wq[kWarps];
+    __shared__ int32_t tau_s[kWarps][kMaxK];
+    __shared__ uint64_t s_wsec[kWarps][2];
+    __shared__ RowRef s_rows[kWarps][kMaxK - 1];
+    __shared__ WarpSets s_ws[kWarps];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        const size_t per = (size_t)scratch_cap * 2 * (sizeof(int32_t) + sizeof(uint64_t));
+        const size_t stride = (per + 255) / 256 * 256;
+        char *base = scratch + stride * ((size_t)blockIdx.x * kWarps + warp);
+        WarpSets &w = s_ws[warp];
+        w.cap = scratch ? scratch_cap : 0;
+        w.xs[0] = (int32_t *)base;
+        w.xs[1] = w.xs[0] + scratch_cap;
+        w.pw[0] = (uint64_t *)(base + (size_t)scratch_cap * 2 * sizeof(int32_t));
+        w.pw[1] = w.pw[0] + scratch_cap;
+        s_wq[warp] = -1;
+    }
+    __syncwarp();
+    const WarpSets &ws = s_ws[warp];
+    const uint32_t total = *n_items_ptr * (uint32_t)kTile;
+    for (;;) {
+        uint32_t c = 0;
+        if (lane == 0) c = atomicAdd(counter, 1u);
+        c = __shfl_sync(kFull, c, 0);
+        if (c >= total) break;
+        const WorkItem it = items[c / kTile];
+        const uint32_t local = c % kTile;
+        if (local >= it.count) continue;
+        if ((int)it.query != s_wq[warp]) {
+            const int words = (int)(sizeof(DevQuery) / sizeof(uint32_t));
+            const uint32_t *qsrc = (const uint32_t *)(queries + it.query);
+            uint32_t *dst = (uint32_t *)&wq[warp];
+            for (int j = lane; j < words; j += 32) dst[j] = qsrc[j];
+            if (lane == 0) s_wq[warp] = (int)it.query;
+            __syncwarp();
+        }
+        const TrialOut r = run_trial<kAnchor, false>(g, wq[warp], it.first + local, tau_s[warp], ws, nullptr,
+                                                     s_wsec[warp], s_rows[warp], lane);
+        if (lane == 0) {
+            const uint64_t k = it.slot * (uint64_t)kTile + local;
+            sv.x[k] = r.x;
+            sv.hit[k] = (uint8_t)r.hit;
+            sv.sec[3 * k] = r.sectors;
+            sv.sec[3 * k + 1] = r.streamed;
+            sv.sec[3 * k + 2] = r.survey;
+        }
+        __syncwarp();
+    }
+}
+
+// One CTA per item (tile) of a scatter epoch: the tile's hit and sector totals and its
+// fixed-order FP64 sums, written to its output slot as the main kernel writes them.
+__global__ void __launch_bounds__(kBlock) tile_reduce_kernel(const WorkItem *__restrict__ items,
+                                                             const uint32_t *__restrict__ n_items_ptr, ScatterView sv,
+                                                             uint64_t *tile_out)
+{
+    __shared__ double xs[kTile];
+    __shared__ double red[kBlock];
+    __shared__ double red2[kBlock];
+    __shared__ unsigned long long s_cnt[4];
+    if (blockIdx.x >= *n_items_ptr) return;
+    const WorkItem it = items[blockIdx.x];
+    if (threadIdx.x < 4) s_cnt[threadIdx.x] = 0;
+    __syncthreads();
+    const uint64_t base = it.slot * (uint64_t)kTile;
+    unsigned long long h = 0, s0 = 0, s1 = 0, s2 = 0;
+    for (int j = threadIdx.x; j < kTile; j += kBlock) {
+        const bool in = (uint32_t)j < it.count;
+        xs[j] = in ? sv.x[base + j] : 0.0;
+        if (in) {
+            h += sv.hit[base + j];
+            s0 += sv.sec[3 * (base + j)];
+            s1 += sv.sec[3 * (base + j) + 1];
+            s2 += sv.sec[3 * (base + j) + 2];
+        }
+    }
+    atomicAdd(&s_cnt[0], h);
+    atomicAdd(&s_cnt[1], s0);
+    atomicAdd(&s_cnt[2], s1);
+    atomicAdd(&s_cnt[3], s2);
+    __syncthreads();
+    tile_fp64_sums(xs, red, red2);
+    if (threadIdx.x == 0) {
+        uint64_t *o = tile_out + kTileWords * it.slot;
+        o[0] = s_cnt[0];
+        o[1] = s_cnt[1];
+        o[2] = (uint64_t)__double_as_longlong(red[0]);
+        o[3] = (uint64_t)__double_as_longlong(red2[0]);
+        o[4] = s_cnt[2];
+        o[5] = s_cnt[3];
+    }
+}
+
 }  // namespace
+
+const void *scatter_function(bool anchor)
+{
+    return anchor ? (const void *)scatter_kernel<true> : (const void *)scatter_kernel<false>;
+}
+
+const void *tile_reduce_function() { return (const void *)tile_reduce_kernel; }
 
 int sampler_occupancy(int *blocks_per_sm)
 {

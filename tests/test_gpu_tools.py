@@ -72,3 +72,44 @@ def test_multi_tile_items_keep_tile_sums(agis):
         assert r["trials"] == n and r["hits"] == int(ts["hits"].sum()) and r["sectors"] == int(ts["sectors"].sum())
         assert r["sectors_streamed"] == int(ts["streamed"].sum()) and r["sectors_survey"] == int(ts["survey"].sum())
         assert r["sum_x"] == acc
+
+
+def test_scatter_epochs_equal_tile_epochs(agis):
+    """An epoch with no more tiles than the grid has CTAs runs in scatter mode (every
+    warp takes single trials, a second kernel reduces each tile); its tile sums must
+    be the main kernel's bits: an estimate of 2^13 trials (32 tiles, one scatter
+    epoch) against agis_sample_device over the same trials (main kernel, one tile
+    per item), for several patterns and modes, plus the batched form."""
+    import torch
+    ctx = agis.Context(0)
+    off, cols = I.rmat_graph(13, 16, seed=6)
+    g = agis.Graph(ctx, off, cols)
+    g.preprocess(1, 2.0 ** -10)
+    n = 1 << 13
+    pats, opts, singles = [], [], []
+    for name, mode in (("4-clique", 0), ("house", 0), ("5-cycle", 1), ("triangle", 2)):
+        p = agis.Pattern(*I.PATTERNS[name])
+        o = agis.default_opts(mode=mode, seed=21, eps=0.0, max_trials=n, chunk_trials=n)
+        r = agis.estimate(g, p, o)
+        assert r["launches"] == 1
+        ntiles = n // agis.TILE
+        out = torch.zeros(ntiles * agis.TILE_WORDS, dtype=torch.int64, device="cuda")
+        agis.sample_device(g, p, o, 0, ntiles, out.data_ptr())
+        torch.cuda.synchronize()
+        ts = agis.tile_sums(out.cpu().numpy().view(np.uint64))
+        acc = acc2 = 0.0
+        for v, v2 in zip(ts["sum_x"], ts["sum_x2"]):
+            acc += float(v)
+            acc2 += float(v2)
+        assert r["sum_x"] == acc and r["sum_x2"] == acc2, name
+        assert r["hits"] == int(ts["hits"].sum()) and r["sectors"] == int(ts["sectors"].sum()), name
+        assert r["sectors_streamed"] == int(ts["streamed"].sum()), name
+        assert r["sectors_survey"] == int(ts["survey"].sum()), name
+        pats.append(p)
+        opts.append(o)
+        singles.append(r)
+    for a, b in zip(singles, agis.estimate_batch(g, pats, opts)):
+        for key in ("trials", "hits", "sectors", "sum_x", "sum_x2"):
+            assert a[key] == b[key], key
+    g.close()
+    ctx.close()
