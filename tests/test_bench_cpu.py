@@ -34,11 +34,11 @@ def test_reference_arm_prints_one_contract_line():
                         "d2h_bytes_per_step": 0}
 
 
-def test_driver_command_fits_its_time_limit():
-    """The round-end command (--gpus 1 --steps 20 --warmup 5) at the stated floor
-    rates: every leg's upper bound (capped queries run to their caps) sums to less
-    than the deadline after which optional legs are skipped, and the deadline leaves
-    room under the 1800 s limit for the CPU baseline and the JSON line."""
+def test_twenty_step_command_fits_its_time_limit():
+    """The 20-step command (--gpus 1 --steps 20 --warmup 5) at the stated floor rates:
+    every leg's upper bound (capped queries run to their caps) sums to less than the
+    deadline after which optional legs are skipped, and the deadline leaves room
+    under an 1800 s limit for the CPU baseline and the JSON line."""
     sys.path.insert(0, ROOT)
     import bench
     args = bench.parse_args(["--gpus", "1", "--steps", "20", "--warmup", "5"])
