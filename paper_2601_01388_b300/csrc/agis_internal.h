@@ -17,6 +17,7 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include "../../include/agis.h"
+#include "agis_device.h"
 
 namespace agis {
 
@@ -28,86 +29,6 @@ struct NvtxRange {
     ~NvtxRange() { nvtxRangePop(); }
     NvtxRange(const NvtxRange &) = delete;
     NvtxRange &operator=(const NvtxRange &) = delete;
-};
-
-constexpr int kMaxK = 8;
-#ifndef AGIS_TILE
-#define AGIS_TILE 256
-#endif
-constexpr int kTile = AGIS_TILE;     // trials per work item (one CTA at a time)
-static_assert(kTile >= 32 && kTile <= 1024 && (kTile & (kTile - 1)) == 0, "tile: power of two in [32, 1024]");
-// A work item covers 1..kMaxSpan consecutive tiles of one query; each tile keeps its
-// own fixed-order reduction and output slot, so results never depend on the span.
-constexpr int kMaxSpan = 4;
-constexpr int kBlock = 256;          // threads per CTA of the sampler
-constexpr int kWarps = kBlock / 32;
-constexpr uint64_t kStreamTrial = 1; // Philox counter word 2 of a trial draw
-constexpr uint64_t kStreamCC = 2;    // ... of a clustering-coefficient probe
-
-// One step of a compiled query as the sampler kernel reads it.
-struct DevStep {
-    int32_t nb;                 // |B[i]|: number of backward neighbours
-    int8_t approx;              // 1: draw with the f_approx weight table (D(i) chose f_approx and
-                                // the weights are not all equal on S_tau); 0: by position / degree
-    int8_t dapprox;             // D(i) itself (1 = f_approx); only the survey's sector count reads it
-    int8_t inc;                 // backward set = previous step's plus the previous vertex
-    int8_t rp_mode;             // pref for |B| = 1: 0 none, 1 per-row prefix of every row,
-                                // 2 prefix of high-degree rows only (located by rp_base)
-    int8_t back[kMaxK];         // step indices of the backward neighbours
-    const uint64_t *q;          // quantised f_approx weight per vertex (approx only)
-    const uint64_t *pref;       // step 0: inclusive prefix over vertices; |B| = 1: row prefix
-};
-
-constexpr int32_t kFlagAnchor = 1;   // DevQuery::flags: anchor draw on several-backward steps
-constexpr int32_t kFlagPlainLists = 2;  // DevQuery::flags: no candidate-list step weighs its survivors
-
-struct DevQuery {
-    int32_t k;
-    int32_t flags;
-    uint64_t seed;
-    uint64_t W1;                // total step-1 weight (f_approx sum or nnz)
-    DevStep step[kMaxK];
-};
-
-// Words of one tile's output (AGIS_TILE_WORDS): hits, model sectors, bits of sum X,
-// bits of sum X^2, streamed part of the model sectors, survey-count sectors.
-constexpr int kTileWords = AGIS_TILE_WORDS;
-
-// A work item: `count` trials (at most kMaxSpan tiles) of query `query` starting at
-// trial `first`; the sums of its t-th tile go to out[kTileWords*(slot+t) ...].
-struct WorkItem {
-    uint32_t query;
-    uint32_t count;
-    uint64_t first;
-    uint64_t slot;
-};
-
-// Where a dump launch writes per-trial records (index = trial - dump_first).
-struct DumpView {
-    int32_t *emb;
-    uint8_t *hit;
-    double *x;
-    uint64_t *sectors;          // 3 words per trial: model total, its streamed part, survey count
-    uint64_t first;
-};
-
-// Per-trial outputs of a scatter epoch (see scatter_kernel), indexed by tile slot *
-// kTile + trial within the tile.
-struct ScatterView {
-    double *x;
-    uint8_t *hit;
-    uint64_t *sec;              // 3 words per trial: sectors, streamed, survey
-};
-
-struct GraphView {
-    const int64_t *off;
-    const int32_t *cols;
-    int64_t nv;
-    int64_t nnz;
-    const int32_t *hub_id;      // per vertex: index of its neighbour bitmap, -1 if none
-    const uint32_t *hub_bits;   // bitmaps, hub_words 32-bit words each
-    int64_t hub_words;
-    const int64_t *rp_base;     // per vertex: start of its row in partial row-prefix tables, -1 if none
 };
 
 struct WeightTable {
@@ -132,8 +53,10 @@ struct LaunchBuffers {
     size_t cap_items = 0;
     uint64_t *d_out = nullptr;  // kTileWords words per tile slot
     size_t cap_out = 0;
-    uint32_t *d_counter = nullptr; // [0] work counter, [1] number of items
-    // per-trial outputs of scatter epochs (trials of up to cap_scatter)
+    // [0] the main kernel's item counter (starts at the number of tail items), [1] the
+    // end of its items; [2] the scatter kernel's trial counter, [3] its number of items
+    uint32_t *d_counter = nullptr;
+    // per-trial outputs of scatter launches (trials of up to cap_scatter)
     double *d_sx = nullptr;
     uint8_t *d_shit = nullptr;
     uint64_t *d_ssec = nullptr;
@@ -153,7 +76,7 @@ struct LaunchBuffers {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaGraphNode_t n_h2d_q = nullptr, n_h2d_i = nullptr, n_h2d_c = nullptr, n_kernel = nullptr,
-                    n_d2h = nullptr;
+                    n_scatter = nullptr, n_reduce = nullptr, n_d2h = nullptr;
     int graph_grid = 0;
     uint64_t generation = 0;       // bumps when device buffers move (graph must be rebuilt)
     uint64_t graph_generation = ~0ull;
@@ -166,6 +89,9 @@ struct LaunchBuffers {
     int sgraph_grid = 0;
     uint64_t sgraph_generation = ~0ull;
     bool sgraph_anchor = false;
+    // stream and events of the tail's scatter launch in epochs of stream launches
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 }  // namespace agis
@@ -240,26 +166,33 @@ void free_table(WeightTable &t);
 // sample.cu: the kernel instance for dumps, or for launches with (anchor) or
 // without anchor-draw queries
 const void *sampler_function(bool dump, bool anchor);
-// launch.cu.  anchor: some staged query uses the anchor draw (selects the instance)
+// launch.cu.  anchor: some staged query uses the anchor draw (selects the instance);
+// urgent: launch at the device's greatest stream priority
 int launch_sampler(agis_graph *g, LaunchBuffers &lb, int grid, const DumpView *dump,
                    cudaStream_t stream, uint64_t implicit_first, uint64_t implicit_count,
-                   uint32_t implicit_span, uint64_t *tile_out, bool anchor);
+                   uint32_t implicit_span, uint64_t *tile_out, bool anchor, bool urgent = false);
 // tiles per work item for an epoch of `tiles` tiles on `grid` CTAs (runtime.cu)
 int span_for(const agis_graph *g, size_t tiles, int grid);
 int add_sampler_node(agis_graph *g, LaunchBuffers &lb, int grid, cudaGraph_t graph,
-                     const cudaGraphNode_t *deps, size_t ndeps, cudaGraphNode_t *node, bool anchor);
+                     const cudaGraphNode_t *deps, size_t ndeps, cudaGraphNode_t *node, bool anchor,
+                     bool urgent = false);
 int sampler_occupancy(int *blocks_per_sm);
 // the scatter kernel instance and the tile reduction of scatter epochs (sample.cu)
 const void *scatter_function(bool anchor);
 const void *tile_reduce_function();
-// launch.cu: a scatter epoch over lb's staged single-tile items (n of them)
-int launch_scatter(agis_graph *g, LaunchBuffers &lb, int grid, size_t n, cudaStream_t stream, bool anchor);
-int add_scatter_nodes(agis_graph *g, LaunchBuffers &lb, int grid, size_t n, cudaGraph_t graph,
+// launch.cu: the scatter kernel on `grid` CTAs over lb's staged tail items (the
+// first lb.d_counter[3] items), its warps' candidate lists after those of the first
+// `scratch_skip` CTAs, then the tile reduction on `rgrid` CTAs (at least one per item)
+int launch_scatter(agis_graph *g, LaunchBuffers &lb, int grid, int scratch_skip, size_t rgrid, cudaStream_t stream,
+                   bool anchor);
+int add_scatter_nodes(agis_graph *g, LaunchBuffers &lb, int grid, int scratch_skip, size_t rgrid, cudaGraph_t graph,
                       const cudaGraphNode_t *deps, size_t ndeps, cudaGraphNode_t *kernel, cudaGraphNode_t *reduce,
                       bool anchor);
-int set_reduce_node_items(LaunchBuffers &lb, cudaGraphExec_t exec, cudaGraphNode_t node, size_t n);
-// an epoch of `tiles` tiles on a grid of `grid` CTAs runs in scatter mode (runtime.cu)
-bool use_scatter(size_t tiles, int grid);
+// the tiles of an epoch of `tiles` tiles on a full grid of `grid` CTAs that the
+// scatter kernel runs (runtime.cu)
+size_t tail_tiles(size_t tiles, int grid);
+// the most tiles tail_tiles returns for that grid
+size_t tail_capacity(int grid);
 int ensure_scatter(LaunchBuffers &lb, size_t tiles);
 
 // runtime.cu

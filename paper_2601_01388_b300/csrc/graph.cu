@@ -425,12 +425,14 @@ int build_hub_bitmaps(agis_graph *g)
         t = std::max<int64_t>(t, sorted[max_hubs - 1] + 1);
     }
     std::vector<int32_t> hubs;
-    std::vector<int32_t> hub_id((size_t)g->nv, -1);
     for (int64_t v = 0; v < g->nv; ++v)
-        if (deg[(size_t)v] >= t && hubs.size() < max_hubs) {
-            hub_id[(size_t)v] = (int32_t)hubs.size();
-            hubs.push_back((int32_t)v);
-        }
+        if (deg[(size_t)v] >= t && hubs.size() < max_hubs) hubs.push_back((int32_t)v);
+    // bitmaps in decreasing degree order (ties by id): the most probed first, so that
+    // one address window covers the hottest of them
+    std::stable_sort(hubs.begin(), hubs.end(),
+                     [&](int32_t a, int32_t b) { return deg[(size_t)a] > deg[(size_t)b]; });
+    std::vector<int32_t> hub_id((size_t)g->nv, -1);
+    for (size_t h = 0; h < hubs.size(); ++h) hub_id[(size_t)hubs[h]] = (int32_t)h;
     g->hub_min_degree = t;
     AGIS_CUDA_TRY(cudaMalloc(&g->hub_id, sizeof(int32_t) * (size_t)g->nv));
     AGIS_CUDA_TRY(cudaMemcpyAsync(g->hub_id, hub_id.data(), sizeof(int32_t) * (size_t)g->nv, cudaMemcpyHostToDevice, st));

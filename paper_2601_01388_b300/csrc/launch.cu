@@ -6,13 +6,22 @@
 
 namespace agis {
 
+// The device's greatest (most urgent) stream priority.
+static int urgent_priority()
+{
+    int least = 0, greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) return 0;
+    return greatest;
+}
+
 // Enqueue one sampler launch over lb's staged queries and items (already on the
-// device; lb.d_counter[0] zeroed and lb.d_counter[1] = number of items).  With
-// implicit_count > 0 the items are implicit runs of implicit_span tiles of query 0
-// (see the kernel).
+// device; lb.d_counter[0] = the first item, lb.d_counter[1] = the end of the items).
+// With implicit_count > 0 the items are implicit runs of implicit_span tiles of query
+// 0 (see the kernel).  An urgent launch gets its CTAs placed before those of a
+// scatter launch enqueued beside it.
 int launch_sampler(agis_graph *g, LaunchBuffers &lb, int grid, const DumpView *dump,
                    cudaStream_t stream, uint64_t implicit_first, uint64_t implicit_count,
-                   uint32_t implicit_span, uint64_t *tile_out, bool anchor)
+                   uint32_t implicit_span, uint64_t *tile_out, bool anchor, bool urgent)
 {
     GraphView gv{g->off, g->cols, g->nv, g->nnz, g->hub_id, g->hub_bits, g->hub_words, g->rp_base};
     DumpView dv = dump ? *dump : DumpView{nullptr, nullptr, nullptr, nullptr, 0};
@@ -26,14 +35,25 @@ int launch_sampler(agis_graph *g, LaunchBuffers &lb, int grid, const DumpView *d
     void *args[] = {&gv, &q, &items, &nptr, &ctr, &out, &dv, &implicit_first, &implicit_count, &implicit_span,
                     &scr, &cap};
     count_launch();
-    return cuda_status(cudaLaunchKernel(sampler_function(dump != nullptr, anchor), dim3(grid), dim3(kBlock),
-                                        args, 0, stream));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kBlock);
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    unsigned na = 0;
+    if (urgent) {
+        attr[na].id = cudaLaunchAttributePriority;
+        attr[na++].val.priority = urgent_priority();
+    }
+    cfg.attrs = na ? attr : nullptr;
+    cfg.numAttrs = na;
+    return cuda_status(cudaLaunchKernelExC(&cfg, sampler_function(dump != nullptr, anchor), args));
 }
 
 // Adds the sampler as a kernel node of a CUDA graph (explicit items, no dump).  The
 // argument values are copied into the node when it is added.
 int add_sampler_node(agis_graph *g, LaunchBuffers &lb, int grid, cudaGraph_t graph,
-                     const cudaGraphNode_t *deps, size_t ndeps, cudaGraphNode_t *node, bool anchor)
+                     const cudaGraphNode_t *deps, size_t ndeps, cudaGraphNode_t *node, bool anchor, bool urgent)
 {
     GraphView gv{g->off, g->cols, g->nv, g->nnz, g->hub_id, g->hub_bits, g->hub_words, g->rp_base};
     DumpView none{nullptr, nullptr, nullptr, nullptr, 0};
@@ -53,86 +73,80 @@ int add_sampler_node(agis_graph *g, LaunchBuffers &lb, int grid, cudaGraph_t gra
     p.blockDim = dim3(kBlock);
     p.sharedMemBytes = 0;
     p.kernelParams = args;
-    return cuda_status(cudaGraphAddKernelNode(node, graph, deps, ndeps, &p));
+    int rc = cuda_status(cudaGraphAddKernelNode(node, graph, deps, ndeps, &p));
+    if (rc != AGIS_OK || !urgent) return rc;
+    cudaKernelNodeAttrValue v = {};
+    v.priority = urgent_priority();
+    return cuda_status(cudaGraphKernelNodeSetAttribute(*node, cudaLaunchAttributePriority, &v));
 }
 
-static void scatter_args(agis_graph *g, LaunchBuffers &lb, GraphView &gv, ScatterView &sv)
-{
-    gv = GraphView{g->off, g->cols, g->nv, g->nnz, g->hub_id, g->hub_bits, g->hub_words, g->rp_base};
-    sv = ScatterView{lb.d_sx, lb.d_shit, lb.d_ssec};
-}
-
-// A scatter epoch: the scatter kernel on `grid` CTAs over the n staged single-tile
-// items (lb.d_counter[0] zeroed, lb.d_counter[1] = n), then one tile-reduction CTA
-// per item, writing lb.d_out.
-int launch_scatter(agis_graph *g, LaunchBuffers &lb, int grid, size_t n, cudaStream_t stream, bool anchor)
-{
+// The scatter kernel's arguments: the tail items are the first lb.d_counter[3] staged
+// items, lb.d_counter[2] its trial counter; its warps' candidate lists follow those
+// of the first `scratch_skip` CTAs (a sampler launch running beside it uses those).
+struct ScatterArgs {
     GraphView gv;
+    const DevQuery *q;
+    const WorkItem *items;
+    const uint32_t *nptr;
+    uint32_t *ctr;
     ScatterView sv;
-    scatter_args(g, lb, gv, sv);
-    const DevQuery *q = lb.d_queries;
-    const WorkItem *items = lb.d_items;
-    const uint32_t *nptr = lb.d_counter + 1;
-    uint32_t *ctr = lb.d_counter;
-    char *scr = (char *)lb.d_scratch;
-    uint32_t cap = lb.scratch_cap;
-    uint64_t *out = lb.d_out;
-    void *args[] = {&gv, &q, &items, &nptr, &ctr, &sv, &scr, &cap};
+    char *scr;
+    uint32_t cap;
+    uint64_t *out;
+    void *args[8];
+    void *rargs[4];
+
+    ScatterArgs(agis_graph *g, LaunchBuffers &lb, int scratch_skip)
+    {
+        gv = GraphView{g->off, g->cols, g->nv, g->nnz, g->hub_id, g->hub_bits, g->hub_words, g->rp_base};
+        q = lb.d_queries;
+        items = lb.d_items;
+        nptr = lb.d_counter + 3;
+        ctr = lb.d_counter + 2;
+        sv = ScatterView{lb.d_sx, lb.d_shit, lb.d_ssec};
+        scr = (char *)lb.d_scratch + scratch_stride(lb.scratch_cap) * (size_t)scratch_skip * kWarps;
+        cap = lb.scratch_cap;
+        out = lb.d_out;
+        void *a[] = {&gv, &q, &items, &nptr, &ctr, &sv, &scr, &cap};
+        void *r[] = {&items, &nptr, &sv, &out};
+        std::copy(a, a + 8, args);
+        std::copy(r, r + 4, rargs);
+    }
+};
+
+// The scatter kernel on `grid` CTAs, then one tile-reduction CTA per tail item
+// (`rgrid` CTAs, those past the items return at once), writing lb.d_out.
+int launch_scatter(agis_graph *g, LaunchBuffers &lb, int grid, int scratch_skip, size_t rgrid, cudaStream_t stream,
+                   bool anchor)
+{
+    ScatterArgs a(g, lb, scratch_skip);
     count_launch();
-    cudaError_t e = cudaLaunchKernel(scatter_function(anchor), dim3(grid), dim3(kBlock), args, 0, stream);
+    cudaError_t e = cudaLaunchKernel(scatter_function(anchor), dim3(grid), dim3(kBlock), a.args, 0, stream);
     if (e != cudaSuccess) return AGIS_ERR_CUDA;
-    void *rargs[] = {&items, &nptr, &sv, &out};
     count_launch();
-    return cuda_status(cudaLaunchKernel(tile_reduce_function(), dim3((unsigned)std::max<size_t>(n, 1)), dim3(kBlock),
-                                        rargs, 0, stream));
+    return cuda_status(cudaLaunchKernel(tile_reduce_function(), dim3((unsigned)std::max<size_t>(rgrid, 1)),
+                                        dim3(kBlock), a.rargs, 0, stream));
 }
 
-// The same two kernels as nodes of a CUDA graph (after deps); the reduction's grid
-// is patched per epoch by set_reduce_node_items.
-int add_scatter_nodes(agis_graph *g, LaunchBuffers &lb, int grid, size_t n, cudaGraph_t graph,
+// The same two kernels as nodes of a CUDA graph (after deps).
+int add_scatter_nodes(agis_graph *g, LaunchBuffers &lb, int grid, int scratch_skip, size_t rgrid, cudaGraph_t graph,
                       const cudaGraphNode_t *deps, size_t ndeps, cudaGraphNode_t *kernel, cudaGraphNode_t *reduce,
                       bool anchor)
 {
-    GraphView gv;
-    ScatterView sv;
-    scatter_args(g, lb, gv, sv);
-    const DevQuery *q = lb.d_queries;
-    const WorkItem *items = lb.d_items;
-    const uint32_t *nptr = lb.d_counter + 1;
-    uint32_t *ctr = lb.d_counter;
-    char *scr = (char *)lb.d_scratch;
-    uint32_t cap = lb.scratch_cap;
-    uint64_t *out = lb.d_out;
-    void *args[] = {&gv, &q, &items, &nptr, &ctr, &sv, &scr, &cap};
+    ScatterArgs a(g, lb, scratch_skip);
     cudaKernelNodeParams p = {};
     p.func = const_cast<void *>(scatter_function(anchor));
     p.gridDim = dim3(grid);
     p.blockDim = dim3(kBlock);
-    p.kernelParams = args;
+    p.kernelParams = a.args;
     cudaError_t e = cudaGraphAddKernelNode(kernel, graph, deps, ndeps, &p);
     if (e != cudaSuccess) return AGIS_ERR_CUDA;
-    void *rargs[] = {&items, &nptr, &sv, &out};
     cudaKernelNodeParams r = {};
     r.func = const_cast<void *>(tile_reduce_function());
-    r.gridDim = dim3((unsigned)std::max<size_t>(n, 1));
+    r.gridDim = dim3((unsigned)std::max<size_t>(rgrid, 1));
     r.blockDim = dim3(kBlock);
-    r.kernelParams = rargs;
+    r.kernelParams = a.rargs;
     return cuda_status(cudaGraphAddKernelNode(reduce, graph, kernel, 1, &r));
-}
-
-int set_reduce_node_items(LaunchBuffers &lb, cudaGraphExec_t exec, cudaGraphNode_t node, size_t n)
-{
-    const WorkItem *items = lb.d_items;
-    const uint32_t *nptr = lb.d_counter + 1;
-    ScatterView sv{lb.d_sx, lb.d_shit, lb.d_ssec};
-    uint64_t *out = lb.d_out;
-    void *rargs[] = {&items, &nptr, &sv, &out};
-    cudaKernelNodeParams r = {};
-    r.func = const_cast<void *>(tile_reduce_function());
-    r.gridDim = dim3((unsigned)std::max<size_t>(n, 1));
-    r.blockDim = dim3(kBlock);
-    r.kernelParams = rargs;
-    return cuda_status(cudaGraphExecKernelNodeSetParams(exec, node, &r));
 }
 
 }  // namespace agis

@@ -13,6 +13,10 @@
 #ifndef AGIS_SAMPLE_SPAN
 #define AGIS_SAMPLE_SPAN 1
 #endif
+// Tail of an epoch larger than the grid, in grids' worth of tiles (see tail_tiles).
+#ifndef AGIS_TAIL_GRIDS
+#define AGIS_TAIL_GRIDS 2
+#endif
 
 namespace agis {
 
@@ -75,6 +79,9 @@ void free_buffers(LaunchBuffers &lb)
     cudaFreeHost(lb.h_items);
     cudaFreeHost(lb.h_out);
     cudaFreeHost(lb.h_counter);
+    if (lb.ev_fork) cudaEventDestroy(lb.ev_fork);
+    if (lb.ev_join) cudaEventDestroy(lb.ev_join);
+    if (lb.aux) cudaStreamDestroy(lb.aux);
     lb = LaunchBuffers();
 }
 
@@ -114,8 +121,8 @@ int ensure_buffers(LaunchBuffers &lb, size_t n_queries, size_t n_items)
     if ((rc = grow_device(&lb.d_items, &lb.cap_items, n_items, &lb.generation))) return rc;
     if ((rc = grow_device(&lb.d_out, &lb.cap_out, kTileWords * n_items, &lb.generation))) return rc;
     if (!lb.d_counter) {
-        AGIS_CUDA_TRY(cudaMalloc(&lb.d_counter, 2 * sizeof(uint32_t)));
-        AGIS_CUDA_TRY(cudaMallocHost(&lb.h_counter, 2 * sizeof(uint32_t)));
+        AGIS_CUDA_TRY(cudaMalloc(&lb.d_counter, 4 * sizeof(uint32_t)));
+        AGIS_CUDA_TRY(cudaMallocHost(&lb.h_counter, 4 * sizeof(uint32_t)));
         ++lb.generation;
     }
     if ((rc = grow_pinned(&lb.h_queries, &lb.hcap_queries, n_queries, &lb.generation))) return rc;
@@ -124,14 +131,26 @@ int ensure_buffers(LaunchBuffers &lb, size_t n_queries, size_t n_items)
     return AGIS_OK;
 }
 
-// An epoch with no more tiles than a full grid has CTAs runs in scatter mode: there
-// every warp of the grid takes single trials (tiles x kTile / warps of them, under
-// 32), where the main kernel would give each of `tiles` CTAs one tile, 32 trials back
-// to back on each warp.  Measured on the benchmark graph: a 4-clique query to +-1%
-// (20,480 trials) 26.3 -> 5.9 ms, a 5-clique (45,056) 56 -> 12.5 ms.
-bool use_scatter(size_t tiles, int grid)
+// The last tiles of an epoch -- as many as a full grid has CTAs, or all of a smaller
+// epoch -- run on the scatter kernel, where every warp of the grid takes single
+// trials.  The main kernel gives a CTA whole tiles, 32 trials back to back on each
+// warp, so an epoch of few tiles leaves most of the GPU idle, and in a larger one the
+// CTAs that run out of tiles wait up to a tile's time for the last ones.  Launched
+// beside the main kernel at a lower priority, the scatter kernel's CTAs take the SM
+// slots that the main kernel's CTAs free as they run out, and its single trials
+// level the end of the epoch.  Measured on the benchmark graph (all of an epoch in
+// scatter mode): a 4-clique query to +-1% (20,480 trials) 26.3 -> 5.9 ms, a
+// 5-clique (45,056) 56 -> 12.5 ms.
+size_t tail_capacity(int grid)
 {
-    return tiles > 0 && tiles <= (size_t)grid;
+    return (size_t)(std::max(1.0, (double)AGIS_TAIL_GRIDS) * (double)std::max(grid, 0));
+}
+
+size_t tail_tiles(size_t tiles, int grid)
+{
+    const size_t full = (size_t)std::max(grid, 0);
+    if (tiles <= full) return tiles;
+    return std::min(tiles, (size_t)(AGIS_TAIL_GRIDS * (double)full));
 }
 
 // Per-trial output buffers of scatter epochs for `tiles` tiles.
@@ -318,7 +337,9 @@ int init_run(agis_graph *g, const agis_pattern *p, const agis_opts *o, QueryRun 
 // min_trials (whole chunks); later ones aim at the trial count Alg. 1's own formula
 // predicts from the sums absorbed so far, N ~ (z sigma / (eps mu))^2, between one
 // chunk and four times the work so far.  Tiles already issued but not absorbed
-// count as work done.
+// count as work done; with some in flight (a server staging its next epoch) a query
+// gets more only when the prediction exceeds them, since tiles past its stopping
+// checkpoint would be computed and discarded.
 static uint64_t tiles_after(const QueryRun &r, uint64_t from)
 {
     const uint64_t left = r.max_tiles > from ? r.max_tiles - from : 0;
@@ -338,6 +359,7 @@ static uint64_t tiles_after(const QueryRun &r, uint64_t from)
         if (var < 0) var = 0;
         double need = mu > 0 ? (r.z * r.z * var) / (r.o.eps * r.o.eps * mu * mu) : 4.0 * issued;
         need = std::min(need, 4.0 * issued + 1.0);
+        if (from > r.done_tiles && need <= issued) return 0;   // the tiles in flight may suffice
         const double more = std::max(need - issued, (double)r.o.chunk_trials);
         want = (uint64_t)std::ceil(more / kTile);
         want = (want + tpc - 1) / tpc * tpc;
@@ -427,31 +449,51 @@ int span_for(const agis_graph *g, size_t tiles, int grid)
     return span;
 }
 
-// Stages items of up to `span` tiles for the given runs (tile ranges) into lb's
-// pinned buffers; tile output slots run 0, 1, ... in query then tile order.
-// Returns the number of items.
-size_t stage_items(LaunchBuffers &lb, std::vector<QueryRun *> &runs, const std::vector<uint64_t> &ntiles, int span)
+// Stages the epoch's work items for the given runs (tile ranges) into lb's pinned
+// buffers and fills lb.h_counter: first the last `tail` tiles (in query then tile
+// order) as single-tile items for the scatter kernel, then the others as items of up
+// to `span` tiles for the main kernel.  Tile output slots run 0, 1, ... in query then
+// tile order.  Returns the number of items.
+size_t stage_items(LaunchBuffers &lb, std::vector<QueryRun *> &runs, const std::vector<uint64_t> &ntiles, int span,
+                   size_t tail)
 {
-    size_t k = 0, m = 0;
+    size_t total = 0;
+    for (uint64_t n : ntiles) total += n;
+    const uint64_t head = total - std::min(tail, total);
+    size_t m = 0;
+    auto emit = [&](size_t q, uint64_t j, uint64_t nt, uint64_t slot) {
+        const QueryRun &r = *runs[q];
+        const uint64_t first = (r.issued_tiles + j) * kTile;
+        WorkItem &w = lb.h_items[m++];
+        w.query = (uint32_t)q;
+        w.count = (uint32_t)std::min<uint64_t>(nt * kTile, r.o.max_trials - first);
+        w.first = first;
+        w.slot = slot;
+    };
+    uint64_t g0 = 0;            // epoch tile index of the query's first tile
     for (size_t q = 0; q < runs.size(); ++q) {
-        QueryRun &r = *runs[q];
-        lb.h_queries[q] = r.dq;
-        for (uint64_t j = 0; j < ntiles[q]; j += (uint64_t)span) {
-            const uint64_t nt = std::min<uint64_t>((uint64_t)span, ntiles[q] - j);
-            const uint64_t first = (r.issued_tiles + j) * kTile;
-            WorkItem &w = lb.h_items[m++];
-            w.query = (uint32_t)q;
-            w.count = (uint32_t)std::min<uint64_t>(nt * kTile, r.o.max_trials - first);
-            w.first = first;
-            w.slot = k;
-            k += nt;
-        }
-        r.issued_tiles += ntiles[q];
+        const uint64_t from = head > g0 ? std::min<uint64_t>(head - g0, ntiles[q]) : 0;
+        for (uint64_t j = from; j < ntiles[q]; ++j) emit(q, j, 1, g0 + j);
+        g0 += ntiles[q];
     }
+    const size_t n_tail = m;
+    g0 = 0;
+    for (size_t q = 0; q < runs.size(); ++q) {
+        const uint64_t nh = head > g0 ? std::min<uint64_t>(head - g0, ntiles[q]) : 0;
+        for (uint64_t j = 0; j < nh; j += (uint64_t)span) emit(q, j, std::min<uint64_t>((uint64_t)span, nh - j), g0 + j);
+        g0 += ntiles[q];
+    }
+    for (size_t q = 0; q < runs.size(); ++q) {
+        lb.h_queries[q] = runs[q]->dq;
+        runs[q]->issued_tiles += ntiles[q];
+    }
+    lb.h_counter[0] = (uint32_t)n_tail;
+    lb.h_counter[1] = (uint32_t)m;
+    lb.h_counter[2] = 0;
+    lb.h_counter[3] = (uint32_t)n_tail;
     return m;
 }
 
-// One epoch by plain stream launches.
 static bool any_anchor(const std::vector<QueryRun *> &runs)
 {
     for (const QueryRun *r : runs)
@@ -459,6 +501,17 @@ static bool any_anchor(const std::vector<QueryRun *> &runs)
     return false;
 }
 
+// The aux stream and fork/join events of lb's tail launches, created on first use.
+static int ensure_aux(LaunchBuffers &lb)
+{
+    if (!lb.aux) AGIS_CUDA_TRY(cudaStreamCreateWithFlags(&lb.aux, cudaStreamNonBlocking));
+    if (!lb.ev_fork) AGIS_CUDA_TRY(cudaEventCreateWithFlags(&lb.ev_fork, cudaEventDisableTiming));
+    if (!lb.ev_join) AGIS_CUDA_TRY(cudaEventCreateWithFlags(&lb.ev_join, cudaEventDisableTiming));
+    return AGIS_OK;
+}
+
+// One epoch by plain stream launches: the main kernel over the head items (urgent),
+// the scatter kernel and tile reduction over the tail on lb.aux beside it.
 int run_epoch_direct(agis_graph *g, std::vector<QueryRun *> &runs, const std::vector<uint64_t> &ntiles,
                      size_t total)
 {
@@ -468,21 +521,29 @@ int run_epoch_direct(agis_graph *g, std::vector<QueryRun *> &runs, const std::ve
     int rc = ensure_buffers(lb, runs.size(), total);
     if (rc != AGIS_OK) return rc;
     const int full = grid_for(g, (size_t)g->ctx->sm_count * 64);
-    const bool scatter = use_scatter(total, full);
-    const size_t n = stage_items(lb, runs, ntiles, scatter ? 1 : span_for(g, total, grid_for(g, total)));
-    lb.h_counter[0] = 0;
-    lb.h_counter[1] = (uint32_t)n;
+    const size_t tail = tail_tiles(total, full);
+    const size_t head = total - tail;
+    const int hgrid = grid_for(g, head);
+    if ((rc = ensure_scratch(g, lb, 2 * full)) != AGIS_OK) return rc;
+    if ((rc = ensure_scatter(lb, tail)) != AGIS_OK) return rc;
+    const size_t n = stage_items(lb, runs, ntiles, head ? span_for(g, head, hgrid) : 1, tail);
+    const size_t n_tail = lb.h_counter[3];
     AGIS_CUDA_TRY(cudaMemcpyAsync(lb.d_queries, lb.h_queries, sizeof(DevQuery) * runs.size(), cudaMemcpyHostToDevice, st));
     AGIS_CUDA_TRY(cudaMemcpyAsync(lb.d_items, lb.h_items, sizeof(WorkItem) * n, cudaMemcpyHostToDevice, st));
-    AGIS_CUDA_TRY(cudaMemcpyAsync(lb.d_counter, lb.h_counter, 2 * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
-    if (scatter) {
-        if ((rc = ensure_scratch(g, lb, full)) != AGIS_OK) return rc;
-        if ((rc = ensure_scatter(lb, n)) != AGIS_OK) return rc;
-        rc = launch_scatter(g, lb, full, n, st, any_anchor(runs));
+    AGIS_CUDA_TRY(cudaMemcpyAsync(lb.d_counter, lb.h_counter, 4 * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
+    const bool anchor = any_anchor(runs);
+    if (head == 0) {
+        rc = launch_scatter(g, lb, full, full, n_tail, st, anchor);
     } else {
-        const int grid = grid_for(g, n);
-        if ((rc = ensure_scratch(g, lb, grid)) != AGIS_OK) return rc;
-        rc = launch_sampler(g, lb, grid, nullptr, st, 0, 0, 1, nullptr, any_anchor(runs));
+        if ((rc = ensure_aux(lb)) != AGIS_OK) return rc;
+        AGIS_CUDA_TRY(cudaEventRecord(lb.ev_fork, st));
+        rc = launch_sampler(g, lb, grid_for(g, n - n_tail), nullptr, st, 0, 0, 1, nullptr, anchor, true);
+        if (rc != AGIS_OK) return rc;
+        AGIS_CUDA_TRY(cudaStreamWaitEvent(lb.aux, lb.ev_fork, 0));
+        rc = launch_scatter(g, lb, full, full, n_tail, lb.aux, anchor);
+        if (rc != AGIS_OK) return rc;
+        AGIS_CUDA_TRY(cudaEventRecord(lb.ev_join, lb.aux));
+        AGIS_CUDA_TRY(cudaStreamWaitEvent(st, lb.ev_join, 0));
     }
     if (rc != AGIS_OK) return rc;
     AGIS_CUDA_TRY(cudaMemcpyAsync(lb.h_out, lb.d_out, sizeof(uint64_t) * kTileWords * total, cudaMemcpyDeviceToHost, st));
@@ -490,10 +551,14 @@ int run_epoch_direct(agis_graph *g, std::vector<QueryRun *> &runs, const std::ve
     return AGIS_OK;
 }
 
-// The batched epoch as a CUDA graph: H2D of queries, items and counters, the
-// persistent sampler, D2H of the tile sums.  Built once per buffer generation and
-// grid; sizes are patched per epoch.  `start` and `done` (either may be null) are
-// recorded around the graph launch.
+// The batched epoch as a CUDA graph: H2D of queries, items and counters, then the
+// main kernel (urgent) beside the scatter kernel and tile reduction of the tail, D2H
+// of the tile sums; an epoch of no more tiles than the grid has CTAs uses a graph
+// without the main kernel.  Each is built once per buffer generation and grid;
+// sizes are patched per epoch.  `start` and `done` (either may be null) are recorded
+// around the graph launch.  The scratch (per-warp candidate lists) of scratch_lb
+// must cover twice the full grid: the main kernel's CTAs use the first half, the
+// scatter kernel's the second.
 int enqueue_epoch_graph(agis_graph *g, LaunchBuffers &lb, const LaunchBuffers &scratch_lb,
                         std::vector<QueryRun *> &runs, const std::vector<uint64_t> &ntiles, size_t total,
                         cudaEvent_t start, cudaEvent_t done)
@@ -502,7 +567,8 @@ int enqueue_epoch_graph(agis_graph *g, LaunchBuffers &lb, const LaunchBuffers &s
     cudaStream_t st = g->ctx->stream;
     int rc = ensure_buffers(lb, runs.size(), total);
     if (rc != AGIS_OK) return rc;
-    const int grid = std::min(grid_for(g, (size_t)g->ctx->sm_count * 64), scratch_lb.scratch_grid);
+    const int grid = std::min(grid_for(g, (size_t)g->ctx->sm_count * 64), scratch_lb.scratch_grid / 2);
+    if (grid <= 0) return AGIS_ERR_ARG;
     if (&lb != &scratch_lb && (lb.d_scratch != scratch_lb.d_scratch || lb.scratch_cap != scratch_lb.scratch_cap)) {
         lb.d_scratch = scratch_lb.d_scratch;
         lb.scratch_cap = scratch_lb.scratch_cap;
@@ -510,83 +576,62 @@ int enqueue_epoch_graph(agis_graph *g, LaunchBuffers &lb, const LaunchBuffers &s
         lb.scratch_borrowed = true;
         ++lb.generation;
     }
+    if ((rc = ensure_scatter(lb, tail_capacity(grid))) != AGIS_OK) return rc;
     const bool anchor = any_anchor(runs);
-    if (use_scatter(total, grid)) {
-        // few tiles: a scatter epoch (its own captured graph)
-        const size_t n = stage_items(lb, runs, ntiles, 1);
-        lb.h_counter[0] = 0;
-        lb.h_counter[1] = (uint32_t)n;
-        if ((rc = ensure_scatter(lb, n)) != AGIS_OK) return rc;
-        if (!lb.sexec || lb.sgraph_generation != lb.generation || lb.sgraph_grid != grid || lb.sgraph_anchor != anchor) {
-            if (lb.sexec) cudaGraphExecDestroy(lb.sexec);
-            if (lb.sgraph) cudaGraphDestroy(lb.sgraph);
-            lb.sexec = nullptr;
-            lb.sgraph = nullptr;
-            AGIS_CUDA_TRY(cudaGraphCreate(&lb.sgraph, 0));
-            AGIS_CUDA_TRY(cudaGraphAddMemcpyNode1D(&lb.s_h2d_q, lb.sgraph, nullptr, 0, lb.d_queries, lb.h_queries,
-                                                   sizeof(DevQuery), cudaMemcpyHostToDevice));
-            AGIS_CUDA_TRY(cudaGraphAddMemcpyNode1D(&lb.s_h2d_i, lb.sgraph, &lb.s_h2d_q, 1, lb.d_items, lb.h_items,
-                                                   sizeof(WorkItem), cudaMemcpyHostToDevice));
-            AGIS_CUDA_TRY(cudaGraphAddMemcpyNode1D(&lb.s_h2d_c, lb.sgraph, &lb.s_h2d_i, 1, lb.d_counter,
-                                                   lb.h_counter, 2 * sizeof(uint32_t), cudaMemcpyHostToDevice));
-            rc = add_scatter_nodes(g, lb, grid, n, lb.sgraph, &lb.s_h2d_c, 1, &lb.s_kernel, &lb.s_reduce, anchor);
-            if (rc != AGIS_OK) return rc;
-            AGIS_CUDA_TRY(cudaGraphAddMemcpyNode1D(&lb.s_d2h, lb.sgraph, &lb.s_reduce, 1, lb.h_out, lb.d_out,
-                                                   kTileWords * sizeof(uint64_t), cudaMemcpyDeviceToHost));
-            AGIS_CUDA_TRY(cudaGraphInstantiate(&lb.sexec, lb.sgraph, 0));
-            lb.sgraph_generation = lb.generation;
-            lb.sgraph_anchor = anchor;
-            lb.sgraph_grid = grid;
-        }
-        AGIS_CUDA_TRY(cudaGraphExecMemcpyNodeSetParams1D(lb.sexec, lb.s_h2d_q, lb.d_queries, lb.h_queries,
-                                                         sizeof(DevQuery) * runs.size(), cudaMemcpyHostToDevice));
-        AGIS_CUDA_TRY(cudaGraphExecMemcpyNodeSetParams1D(lb.sexec, lb.s_h2d_i, lb.d_items, lb.h_items,
-                                                         sizeof(WorkItem) * std::max<size_t>(n, 1),
-                                                         cudaMemcpyHostToDevice));
-        if ((rc = set_reduce_node_items(lb, lb.sexec, lb.s_reduce, n)) != AGIS_OK) return rc;
-        AGIS_CUDA_TRY(cudaGraphExecMemcpyNodeSetParams1D(lb.sexec, lb.s_d2h, lb.h_out, lb.d_out,
-                                                         sizeof(uint64_t) * kTileWords * std::max<size_t>(total, 1),
-                                                         cudaMemcpyDeviceToHost));
-        if (start) AGIS_CUDA_TRY(cudaEventRecord(start, st));
-        count_launch(2);
-        AGIS_CUDA_TRY(cudaGraphLaunch(lb.sexec, st));
-        if (done) AGIS_CUDA_TRY(cudaEventRecord(done, st));
-        return AGIS_OK;
-    }
-    const size_t n = stage_items(lb, runs, ntiles, span_for(g, total, grid));
-    lb.h_counter[0] = 0;
-    lb.h_counter[1] = (uint32_t)n;
-    if (!lb.exec || lb.graph_generation != lb.generation || lb.graph_grid != grid || lb.graph_anchor != anchor) {
-        if (lb.exec) cudaGraphExecDestroy(lb.exec);
-        if (lb.graph) cudaGraphDestroy(lb.graph);
-        lb.exec = nullptr;
-        lb.graph = nullptr;
-        AGIS_CUDA_TRY(cudaGraphCreate(&lb.graph, 0));
-        AGIS_CUDA_TRY(cudaGraphAddMemcpyNode1D(&lb.n_h2d_q, lb.graph, nullptr, 0, lb.d_queries, lb.h_queries,
+    const size_t tail = tail_tiles(total, grid);
+    const size_t head = total - tail;
+    const size_t n = stage_items(lb, runs, ntiles, head ? span_for(g, head, grid) : 1, tail);
+    const bool mixed = head > 0;
+    cudaGraph_t &graph = mixed ? lb.graph : lb.sgraph;
+    cudaGraphExec_t &exec = mixed ? lb.exec : lb.sexec;
+    cudaGraphNode_t &h2d_q = mixed ? lb.n_h2d_q : lb.s_h2d_q;
+    cudaGraphNode_t &h2d_i = mixed ? lb.n_h2d_i : lb.s_h2d_i;
+    cudaGraphNode_t &h2d_c = mixed ? lb.n_h2d_c : lb.s_h2d_c;
+    cudaGraphNode_t &d2h = mixed ? lb.n_d2h : lb.s_d2h;
+    uint64_t &gen = mixed ? lb.graph_generation : lb.sgraph_generation;
+    int &ggrid = mixed ? lb.graph_grid : lb.sgraph_grid;
+    bool &ganchor = mixed ? lb.graph_anchor : lb.sgraph_anchor;
+    if (!exec || gen != lb.generation || ggrid != grid || ganchor != anchor) {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        exec = nullptr;
+        graph = nullptr;
+        AGIS_CUDA_TRY(cudaGraphCreate(&graph, 0));
+        AGIS_CUDA_TRY(cudaGraphAddMemcpyNode1D(&h2d_q, graph, nullptr, 0, lb.d_queries, lb.h_queries,
                                                sizeof(DevQuery), cudaMemcpyHostToDevice));
-        AGIS_CUDA_TRY(cudaGraphAddMemcpyNode1D(&lb.n_h2d_i, lb.graph, &lb.n_h2d_q, 1, lb.d_items, lb.h_items,
-                                               sizeof(WorkItem), cudaMemcpyHostToDevice));
-        AGIS_CUDA_TRY(cudaGraphAddMemcpyNode1D(&lb.n_h2d_c, lb.graph, &lb.n_h2d_i, 1, lb.d_counter, lb.h_counter,
-                                               2 * sizeof(uint32_t), cudaMemcpyHostToDevice));
-        rc = add_sampler_node(g, lb, grid, lb.graph, &lb.n_h2d_c, 1, &lb.n_kernel, anchor);
+        AGIS_CUDA_TRY(cudaGraphAddMemcpyNode1D(&h2d_i, graph, &h2d_q, 1, lb.d_items, lb.h_items, sizeof(WorkItem),
+                                               cudaMemcpyHostToDevice));
+        AGIS_CUDA_TRY(cudaGraphAddMemcpyNode1D(&h2d_c, graph, &h2d_i, 1, lb.d_counter, lb.h_counter,
+                                               4 * sizeof(uint32_t), cudaMemcpyHostToDevice));
+        cudaGraphNode_t ends[2];
+        size_t nends = 0;
+        if (mixed) {
+            rc = add_sampler_node(g, lb, grid, graph, &h2d_c, 1, &lb.n_kernel, anchor, true);
+            if (rc != AGIS_OK) return rc;
+            ends[nends++] = lb.n_kernel;
+        }
+        cudaGraphNode_t &skernel = mixed ? lb.n_scatter : lb.s_kernel;
+        cudaGraphNode_t &reduce = mixed ? lb.n_reduce : lb.s_reduce;
+        rc = add_scatter_nodes(g, lb, grid, grid, tail_capacity(grid), graph, &h2d_c, 1, &skernel, &reduce, anchor);
         if (rc != AGIS_OK) return rc;
-        AGIS_CUDA_TRY(cudaGraphAddMemcpyNode1D(&lb.n_d2h, lb.graph, &lb.n_kernel, 1, lb.h_out, lb.d_out,
+        ends[nends++] = reduce;
+        AGIS_CUDA_TRY(cudaGraphAddMemcpyNode1D(&d2h, graph, ends, nends, lb.h_out, lb.d_out,
                                                kTileWords * sizeof(uint64_t), cudaMemcpyDeviceToHost));
-        AGIS_CUDA_TRY(cudaGraphInstantiate(&lb.exec, lb.graph, 0));
-        lb.graph_generation = lb.generation;
-        lb.graph_anchor = anchor;
-        lb.graph_grid = grid;
+        AGIS_CUDA_TRY(cudaGraphInstantiate(&exec, graph, 0));
+        gen = lb.generation;
+        ganchor = anchor;
+        ggrid = grid;
     }
-    AGIS_CUDA_TRY(cudaGraphExecMemcpyNodeSetParams1D(lb.exec, lb.n_h2d_q, lb.d_queries, lb.h_queries,
+    AGIS_CUDA_TRY(cudaGraphExecMemcpyNodeSetParams1D(exec, h2d_q, lb.d_queries, lb.h_queries,
                                                      sizeof(DevQuery) * runs.size(), cudaMemcpyHostToDevice));
-    AGIS_CUDA_TRY(cudaGraphExecMemcpyNodeSetParams1D(lb.exec, lb.n_h2d_i, lb.d_items, lb.h_items,
+    AGIS_CUDA_TRY(cudaGraphExecMemcpyNodeSetParams1D(exec, h2d_i, lb.d_items, lb.h_items,
                                                      sizeof(WorkItem) * std::max<size_t>(n, 1), cudaMemcpyHostToDevice));
-    AGIS_CUDA_TRY(cudaGraphExecMemcpyNodeSetParams1D(lb.exec, lb.n_d2h, lb.h_out, lb.d_out,
+    AGIS_CUDA_TRY(cudaGraphExecMemcpyNodeSetParams1D(exec, d2h, lb.h_out, lb.d_out,
                                                      sizeof(uint64_t) * kTileWords * std::max<size_t>(total, 1),
                                                      cudaMemcpyDeviceToHost));
     if (start) AGIS_CUDA_TRY(cudaEventRecord(start, st));
-    count_launch();
-    AGIS_CUDA_TRY(cudaGraphLaunch(lb.exec, st));
+    count_launch(mixed ? 3 : 2);
+    AGIS_CUDA_TRY(cudaGraphLaunch(exec, st));
     if (done) AGIS_CUDA_TRY(cudaEventRecord(done, st));
     return AGIS_OK;
 }
@@ -596,7 +641,7 @@ int run_epoch_graph(agis_graph *g, std::vector<QueryRun *> &runs, const std::vec
 {
     LaunchBuffers &lb = g->lb;
     const int grid = grid_for(g, (size_t)g->ctx->sm_count * 64);
-    int rc = ensure_scratch(g, lb, grid);
+    int rc = ensure_scratch(g, lb, 2 * grid);
     if (rc != AGIS_OK) return rc;
     rc = enqueue_epoch_graph(g, lb, lb, runs, ntiles, total, nullptr, nullptr);
     if (rc != AGIS_OK) return rc;

@@ -1097,13 +1097,14 @@ __global__ void __launch_bounds__(kBlock, AGIS_MIN_BLOCKS) sample_kernel(GraphVi
     }
 }
 
-// Scatter epochs (epochs of few tiles, e.g. a query's first Alg. 1 checkpoints): in
-// the main kernel one CTA runs a whole tile, 32 trials per warp in sequence, so such
-// an epoch takes as long as 32 trials back to back on an almost idle GPU.  Here every
-// warp of a full grid pulls single trials from the device counter (trial c of the
-// epoch is trial c mod kTile of item c / kTile; items are single tiles) and writes
-// its output to per-trial buffers; tile_reduce_kernel then forms each tile's sums
-// with the main kernel's fixed-order reduction, so the results are the same bits.
+// Scatter epochs (epochs of few tiles, e.g. a query's first Alg. 1 checkpoints, and
+// the last grid-full of tiles of larger ones): in the main kernel one CTA runs a
+// whole tile, 32 trials per warp in sequence, so such tiles take as long as 32 trials
+// back to back on an almost idle GPU.  Here every warp of a full grid pulls single
+// trials from the device counter (trial c is trial c mod kTile of item c / kTile;
+// items are single tiles) and writes its output to per-trial buffers at index c;
+// tile_reduce_kernel then forms each tile's sums with the main kernel's fixed-order
+// reduction, so the results are the same bits.
 template <bool kAnchor>
 __global__ void __launch_bounds__(kBlock, AGIS_MIN_BLOCKS) scatter_kernel(GraphView g, const DevQuery *__restrict__ queries,
                                                          const WorkItem *__restrict__ items,
@@ -1152,7 +1153,7 @@ __global__ void __launch_bounds__(kBlock, AGIS_MIN_BLOCKS) scatter_kernel(GraphV
         const TrialOut r = run_trial<kAnchor, false>(g, wq[warp], it.first + local, tau_s[warp], ws, nullptr,
                                                      s_wsec[warp], s_rows[warp], lane);
         if (lane == 0) {
-            const uint64_t k = it.slot * (uint64_t)kTile + local;
+            const uint64_t k = c;          // = item * kTile + trial within the tile
             sv.x[k] = r.x;
             sv.hit[k] = (uint8_t)r.hit;
             sv.sec[3 * k] = r.sectors;
@@ -1177,7 +1178,7 @@ __global__ void __launch_bounds__(kBlock) tile_reduce_kernel(const WorkItem *__r
     const WorkItem it = items[blockIdx.x];
     if (threadIdx.x < 4) s_cnt[threadIdx.x] = 0;
     __syncthreads();
-    const uint64_t base = it.slot * (uint64_t)kTile;
+    const uint64_t base = (uint64_t)blockIdx.x * kTile;
     unsigned long long h = 0, s0 = 0, s1 = 0, s2 = 0;
     for (int j = threadIdx.x; j < kTile; j += kBlock) {
         const bool in = (uint32_t)j < it.count;

@@ -205,7 +205,7 @@ bool launch_epoch(agis_server *s, std::deque<Epoch> &inflight, int &rc)
     if (e.runs.empty()) return false;
     e.slot = (int)(s->launched & 1);
     e.index = s->launched;
-    rc = ensure_scratch(g, s->lb[0], grid);
+    rc = ensure_scratch(g, s->lb[0], 2 * grid);
     if (rc == AGIS_OK)
         rc = enqueue_epoch_graph(g, s->lb[e.slot], s->lb[0], e.runs, e.ntiles, total, s->ev_start[e.slot],
                                  s->ev_done[e.slot]);

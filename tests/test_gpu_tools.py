@@ -113,3 +113,68 @@ def test_scatter_epochs_equal_tile_epochs(agis):
             assert a[key] == b[key], key
     g.close()
     ctx.close()
+
+
+def _device_tile_sums(agis, g, p, o, ntiles):
+    """The main kernel's tile sums of trials [0, ntiles * TILE), folded in tile order
+    as the Alg. 1 loop folds them."""
+    import torch
+    out = torch.zeros(ntiles * agis.TILE_WORDS, dtype=torch.int64, device="cuda")
+    agis.sample_device(g, p, o, 0, ntiles, out.data_ptr())
+    torch.cuda.synchronize()
+    ts = agis.tile_sums(out.cpu().numpy().view(np.uint64))
+    acc = acc2 = 0.0
+    for v, v2 in zip(ts["sum_x"], ts["sum_x2"]):
+        acc += float(v)
+        acc2 += float(v2)
+    return {"sum_x": acc, "sum_x2": acc2, "hits": int(ts["hits"].sum()), "sectors": int(ts["sectors"].sum()),
+            "sectors_streamed": int(ts["streamed"].sum()), "sectors_survey": int(ts["survey"].sum())}
+
+
+def test_head_and_tail_epochs_equal_tile_epochs(agis, oracle_mod):
+    """An epoch of more tiles than the grid has CTAs runs its last grid-full of tiles
+    on the scatter kernel beside the main kernel; no tile's sums may depend on which
+    of the two ran it.  One epoch of 1172 tiles (the grid has 740 CTAs on 148 SMs)
+    against agis_sample_device over the same tiles, for several patterns and modes; a
+    batch of three 400-tile queries, whose tail covers the second query's end and all
+    of the third; and a ragged 300,000-trial epoch against the oracle's sums."""
+    ctx = agis.Context(0)
+    off, cols = I.rmat_graph(13, 16, seed=6)
+    g = agis.Graph(ctx, off, cols)
+    g.preprocess(1, 2.0 ** -10)
+    T = agis.TILE
+    keys = ("hits", "sectors", "sectors_streamed", "sectors_survey", "sum_x", "sum_x2")
+    for name, mode in (("4-clique", 0), ("house", 1), ("5-cycle", 2)):
+        p = agis.Pattern(*I.PATTERNS[name])
+        o = agis.default_opts(mode=mode, seed=23, eps=0.0, max_trials=1172 * T, chunk_trials=1172 * T)
+        r = agis.estimate(g, p, o)
+        assert r["launches"] == 1 and r["trials"] == 1172 * T
+        d = _device_tile_sums(agis, g, p, o, 1172)
+        for key in keys:
+            assert r[key] == d[key], (name, key)
+        rb = agis.estimate_batch(g, [p], [o])[0]
+        for key in keys:
+            assert rb[key] == d[key], (name, key)
+    pats = [agis.Pattern(*I.PATTERNS[n]) for n in ("4-clique", "house", "5-cycle")]
+    opts = [agis.default_opts(mode=m, seed=30 + m, eps=0.0, max_trials=400 * T, chunk_trials=400 * T)
+            for m in range(3)]
+    batch = agis.estimate_batch(g, pats, opts)
+    for p, o, b in zip(pats, opts, batch):
+        d = _device_tile_sums(agis, g, p, o, 400)
+        single = agis.estimate(g, p, o)
+        for key in keys:
+            assert b[key] == d[key] == single[key], key
+    # ragged last tile, against the oracle
+    nsum, hits = oracle_mod.graph_stats(off, cols, 1)
+    k, edges = I.PATTERNS["house"]
+    n = 300000
+    o = agis.default_opts(mode=0, seed=41, eps=0.0, max_trials=n, chunk_trials=n // 1024 * 1024)
+    r = agis.estimate(g, agis.Pattern(k, edges), o)
+    s = oracle_mod.Query(off, cols, k, edges, nsum=nsum, hits=hits, mode=0, seed=41).sums(0, n)
+    assert r["trials"] == n
+    for key in keys[:4]:
+        assert r[key] == s[key], key
+    assert r["sum_x"] == pytest.approx(s["sum_x"], rel=1e-9, abs=0)
+    assert r["sum_x2"] == pytest.approx(s["sum_x2"], rel=1e-9, abs=0)
+    g.close()
+    ctx.close()
