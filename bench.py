@@ -240,9 +240,10 @@ def measured_peaks():
 
 
 def kernel_source_hash():
-    """sha256[:16] over the sampler's sources (kernel, the definitions it reads, RNG)."""
+    """sha256[:16] over the sampler's sources (kernel, the definitions it reads, RNG,
+    and its launches, which set the persisting-L2 window)."""
     h = hashlib.sha256()
-    for f in ("sample.cu", "agis_device.h", "philox.cuh"):
+    for f in ("sample.cu", "agis_device.h", "philox.cuh", "launch.cu"):
         h.update(open(os.path.join(ROOT, "paper_2601_01388_b300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 

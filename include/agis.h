@@ -205,6 +205,17 @@ int agis_graph_is_oriented(const agis_graph *g);
 int agis_graph_set_memory_policy(agis_graph *g, uint64_t row_prefix_bytes, uint64_t bitmap_bytes,
                                  int64_t bitmap_min_degree, uint32_t list_entries);
 
+/* agis_graph_set_l2_window: bytes of g's hub neighbour bitmaps that sampler launches
+ * on g mark as persisting in L2 (a CUDA access-policy window over the bitmaps, which
+ * are laid out in decreasing degree order, so the window holds the most probed
+ * ones); default 48 MiB, limited by the device's largest window and persisting
+ * set-aside (79 MiB on a B300); 0 turns the window off.  The first windowed launch
+ * raises the context's persisting-L2 set-aside to the window's size, which leaves
+ * other kernels of the process that much less L2 while the agis_ctx lives; its
+ * release restores the previous set-aside.  No effect without hub bitmaps.
+ * Results never depend on this setting.  Errors: ARG (NULL). */
+int agis_graph_set_l2_window(agis_graph *g, uint64_t bytes);
+
 /* ---- preprocessing cache ---------------------------------------------------
  * The System Overview runs the preprocessor only for a graph that has not been
  * preprocessed yet; these calls keep that work across processes.

@@ -28,7 +28,7 @@ MODE_AUTO, MODE_APPROX, MODE_UNIFORM = 0, 1, 2
 EXPORTS = [
     "agis_status_str", "agis_default_opts", "agis_create", "agis_destroy", "agis_graph_load_csr",
     "agis_graph_preprocess", "agis_graph_info", "agis_graph_stats_copy", "agis_graph_weight_table",
-    "agis_graph_row_prefix", "agis_graph_orient", "agis_graph_is_oriented", "agis_graph_set_memory_policy", "agis_graph_validate", "agis_graph_copy_csr", "agis_graph_drop_tables", "agis_graph_free", "agis_graph_generate_rmat", "agis_graph_generate_chunglu",
+    "agis_graph_row_prefix", "agis_graph_orient", "agis_graph_is_oriented", "agis_graph_set_memory_policy", "agis_graph_set_l2_window", "agis_graph_validate", "agis_graph_copy_csr", "agis_graph_drop_tables", "agis_graph_free", "agis_graph_generate_rmat", "agis_graph_generate_chunglu",
     "agis_pattern_create", "agis_pattern_info", "agis_pattern_decide", "agis_pattern_free",
     "agis_estimate", "agis_estimate_batch", "agis_autotune", "agis_dump_trials", "agis_sample_device",
     "agis_prepare", "agis_tile_trials", "agis_z_of_delta", "agis_kernel_launches", "agis_prefix_sum_u64_noalloc", "agis_probe_random_read", "agis_step_timers", "agis_server_create", "agis_server_submit", "agis_server_poll",
@@ -70,6 +70,7 @@ _sig = {
     "agis_graph_weight_table": ([VP, P(C.c_int32), VP, VP, P(C.c_int32)], C.c_int),
     "agis_graph_row_prefix": ([VP, P(C.c_int32), VP], C.c_int),
     "agis_graph_set_memory_policy": ([VP, C.c_uint64, C.c_uint64, C.c_int64, C.c_uint32], C.c_int),
+    "agis_graph_set_l2_window": ([VP, C.c_uint64], C.c_int),
     "agis_graph_validate": ([VP], C.c_int),
     "agis_graph_orient": ([VP, P(VP)], C.c_int),
     "agis_graph_is_oriented": ([VP], C.c_int),
@@ -334,6 +335,10 @@ class Graph:
     def set_memory_policy(self, row_prefix_bytes=0, bitmap_bytes=0, bitmap_min_degree=0, list_entries=0):
         _check(_lib.agis_graph_set_memory_policy(self.h, row_prefix_bytes, bitmap_bytes, bitmap_min_degree,
                                                  list_entries), "agis_graph_set_memory_policy")
+
+    def set_l2_window(self, nbytes):
+        """Bytes of hub bitmaps kept persisting in L2 by sampler launches (0: off)."""
+        _check(_lib.agis_graph_set_l2_window(self.h, nbytes), "agis_graph_set_l2_window")
 
     def validate(self):
         _check(_lib.agis_graph_validate(self.h), "agis_graph_validate")

@@ -89,6 +89,7 @@ struct LaunchBuffers {
     int sgraph_grid = 0;
     uint64_t sgraph_generation = ~0ull;
     bool sgraph_anchor = false;
+    uint64_t graph_l2 = ~0ull, sgraph_l2 = ~0ull;  // the L2 window the cached graphs were built with
     // stream and events of the tail's scatter launch in epochs of stream launches
     cudaStream_t aux = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -103,6 +104,8 @@ struct agis_ctx {
     bool own_stream = false;
     int sm_count = 0;
     int blocks_per_sm = 0;      // sampler CTAs per SM chosen by the autotuner (0 = not tuned)
+    bool l2_limit_set = false;  // the persisting-L2 set-aside was raised (restored at release)
+    size_t l2_limit_before = 0;
     int span = 0;               // tiles per work item chosen by the autotuner (0 = not tuned)
 };
 
@@ -147,6 +150,9 @@ struct agis_graph {
     int64_t hub_words = 0;
     int64_t n_hubs = 0;
     int64_t hub_min_degree = 0;
+    // bytes of hub bitmaps (highest degrees first) kept persisting in L2 by sampler
+    // launches (agis_graph_set_l2_window)
+    uint64_t l2_window_bytes = 48ull << 20;
 };
 
 namespace agis {

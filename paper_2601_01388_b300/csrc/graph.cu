@@ -855,6 +855,7 @@ extern "C" int agis_graph_orient(agis_graph *g, agis_graph **out)
     o->bitmap_budget = g->bitmap_budget;
     o->bitmap_min_degree = g->bitmap_min_degree;
     o->list_cap = g->list_cap;
+    o->l2_window_bytes = g->l2_window_bytes;
     uint64_t *kept = nullptr;
     auto fail = [&](int rc) {
         cudaStreamSynchronize(st);
@@ -1024,5 +1025,14 @@ extern "C" int agis_graph_set_memory_policy(agis_graph *g, uint64_t row_prefix_b
         g->rp_nrows = g->rp_entries = g->rp_min_degree = 0;
     }
     g->lb.generation++;
+    return AGIS_OK;
+}
+
+extern "C" int agis_graph_set_l2_window(agis_graph *g, uint64_t bytes)
+{
+    if (!g) return AGIS_ERR_ARG;
+    std::lock_guard<std::recursive_mutex> lk(g->mu);
+    g->l2_window_bytes = bytes;
+    g->lb.generation++;          // captured epoch graphs carry the window as a node attribute
     return AGIS_OK;
 }

@@ -6,6 +6,52 @@
 
 namespace agis {
 
+// The persisting-L2 access window of sampler launches on g: its hub bitmaps, laid out
+// in decreasing degree order, up to g->l2_window_bytes (within the device's window
+// and set-aside limits).  Probes of the hottest hubs' bitmaps are the sampler's most
+// frequent random sectors; marked persisting they stay in L2 instead of competing
+// with the streamed rows.  The context's set-aside is raised to the window's size at
+// the first such launch and restored when the context is released.  Returns false
+// (no window) when off, without hubs, or when the device has no set-aside.
+static bool l2_window(agis_graph *g, cudaAccessPolicyWindow *w)
+{
+    if (g->l2_window_bytes == 0 || !g->hub_bits || g->n_hubs <= 0) return false;
+    agis_ctx *c = g->ctx;
+    int max_set = 0, max_win = 0;
+    if (cudaDeviceGetAttribute(&max_set, cudaDevAttrMaxPersistingL2CacheSize, c->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&max_win, cudaDevAttrMaxAccessPolicyWindowSize, c->device) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (max_set <= 0 || max_win <= 0) return false;
+    size_t want = (size_t)g->l2_window_bytes;
+    want = std::min(want, (size_t)g->n_hubs * (size_t)g->hub_words * sizeof(uint32_t));
+    want = std::min(want, (size_t)max_win);
+    want = std::min(want, (size_t)max_set);
+    if (want == 0) return false;
+    size_t cur = 0;
+    if (cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (cur < want) {
+        if (!c->l2_limit_set) {
+            c->l2_limit_before = cur;
+            c->l2_limit_set = true;
+        }
+        if (cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+    }
+    w->base_ptr = (void *)g->hub_bits;
+    w->num_bytes = want;
+    w->hitRatio = 1.0f;
+    w->hitProp = cudaAccessPropertyPersisting;
+    w->missProp = cudaAccessPropertyStreaming;
+    return true;
+}
+
 // The device's greatest (most urgent) stream priority.
 static int urgent_priority()
 {
@@ -39,11 +85,16 @@ int launch_sampler(agis_graph *g, LaunchBuffers &lb, int grid, const DumpView *d
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(kBlock);
     cfg.stream = stream;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     unsigned na = 0;
     if (urgent) {
         attr[na].id = cudaLaunchAttributePriority;
         attr[na++].val.priority = urgent_priority();
+    }
+    cudaAccessPolicyWindow w;
+    if (l2_window(g, &w)) {
+        attr[na].id = cudaLaunchAttributeAccessPolicyWindow;
+        attr[na++].val.accessPolicyWindow = w;
     }
     cfg.attrs = na ? attr : nullptr;
     cfg.numAttrs = na;
@@ -74,7 +125,12 @@ int add_sampler_node(agis_graph *g, LaunchBuffers &lb, int grid, cudaGraph_t gra
     p.sharedMemBytes = 0;
     p.kernelParams = args;
     int rc = cuda_status(cudaGraphAddKernelNode(node, graph, deps, ndeps, &p));
-    if (rc != AGIS_OK || !urgent) return rc;
+    if (rc != AGIS_OK) return rc;
+    cudaKernelNodeAttrValue w = {};
+    if (l2_window(g, &w.accessPolicyWindow) &&
+        (rc = cuda_status(cudaGraphKernelNodeSetAttribute(*node, cudaLaunchAttributeAccessPolicyWindow, &w))) != AGIS_OK)
+        return rc;
+    if (!urgent) return rc;
     cudaKernelNodeAttrValue v = {};
     v.priority = urgent_priority();
     return cuda_status(cudaGraphKernelNodeSetAttribute(*node, cudaLaunchAttributePriority, &v));
@@ -121,7 +177,17 @@ int launch_scatter(agis_graph *g, LaunchBuffers &lb, int grid, int scratch_skip,
 {
     ScatterArgs a(g, lb, scratch_skip);
     count_launch();
-    cudaError_t e = cudaLaunchKernel(scatter_function(anchor), dim3(grid), dim3(kBlock), a.args, 0, stream);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kBlock);
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    if (l2_window(g, &attr[0].val.accessPolicyWindow)) {
+        attr[0].id = cudaLaunchAttributeAccessPolicyWindow;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+    }
+    cudaError_t e = cudaLaunchKernelExC(&cfg, scatter_function(anchor), a.args);
     if (e != cudaSuccess) return AGIS_ERR_CUDA;
     count_launch();
     return cuda_status(cudaLaunchKernel(tile_reduce_function(), dim3((unsigned)std::max<size_t>(rgrid, 1)),
@@ -141,6 +207,10 @@ int add_scatter_nodes(agis_graph *g, LaunchBuffers &lb, int grid, int scratch_sk
     p.kernelParams = a.args;
     cudaError_t e = cudaGraphAddKernelNode(kernel, graph, deps, ndeps, &p);
     if (e != cudaSuccess) return AGIS_ERR_CUDA;
+    cudaKernelNodeAttrValue v = {};
+    if (l2_window(g, &v.accessPolicyWindow) &&
+        cudaGraphKernelNodeSetAttribute(*kernel, cudaLaunchAttributeAccessPolicyWindow, &v) != cudaSuccess)
+        return AGIS_ERR_CUDA;
     cudaKernelNodeParams r = {};
     r.func = const_cast<void *>(tile_reduce_function());
     r.gridDim = dim3((unsigned)std::max<size_t>(rgrid, 1));

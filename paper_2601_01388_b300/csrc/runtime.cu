@@ -15,7 +15,7 @@
 #endif
 // Tail of an epoch larger than the grid, in grids' worth of tiles (see tail_tiles).
 #ifndef AGIS_TAIL_GRIDS
-#define AGIS_TAIL_GRIDS 2
+#define AGIS_TAIL_GRIDS 8
 #endif
 
 namespace agis {
@@ -591,7 +591,8 @@ int enqueue_epoch_graph(agis_graph *g, LaunchBuffers &lb, const LaunchBuffers &s
     uint64_t &gen = mixed ? lb.graph_generation : lb.sgraph_generation;
     int &ggrid = mixed ? lb.graph_grid : lb.sgraph_grid;
     bool &ganchor = mixed ? lb.graph_anchor : lb.sgraph_anchor;
-    if (!exec || gen != lb.generation || ggrid != grid || ganchor != anchor) {
+    uint64_t &gl2 = mixed ? lb.graph_l2 : lb.sgraph_l2;
+    if (!exec || gen != lb.generation || ggrid != grid || ganchor != anchor || gl2 != g->l2_window_bytes) {
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
         exec = nullptr;
@@ -621,6 +622,7 @@ int enqueue_epoch_graph(agis_graph *g, LaunchBuffers &lb, const LaunchBuffers &s
         gen = lb.generation;
         ganchor = anchor;
         ggrid = grid;
+        gl2 = g->l2_window_bytes;
     }
     AGIS_CUDA_TRY(cudaGraphExecMemcpyNodeSetParams1D(exec, h2d_q, lb.d_queries, lb.h_queries,
                                                      sizeof(DevQuery) * runs.size(), cudaMemcpyHostToDevice));
@@ -783,6 +785,12 @@ void ctx_release(agis_ctx *c)
 {
     if (c->refs.fetch_sub(1) != 1) return;
     cudaSetDevice(c->device);
+    if (c->l2_limit_set) {
+        // the persisting-L2 set-aside as it was before the first windowed launch
+        cudaCtxResetPersistingL2Cache();
+        cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, c->l2_limit_before);
+        cudaGetLastError();
+    }
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
 }
@@ -797,6 +805,8 @@ void graph_release(agis_graph *g)
         std::lock_guard<std::recursive_mutex> lk(g->mu);
         cudaSetDevice(c->device);
         cudaStreamSynchronize(c->stream);
+        // lines of the bitmaps marked persisting go back to normal before their memory does
+        if (c->l2_limit_set && g->hub_bits) cudaCtxResetPersistingL2Cache();
         for (auto &kv : g->tables) free_table(kv.second);
         g->tables.clear();
         free_buffers(g->lb);

@@ -178,3 +178,32 @@ def test_head_and_tail_epochs_equal_tile_epochs(agis, oracle_mod):
     assert r["sum_x2"] == pytest.approx(s["sum_x2"], rel=1e-9, abs=0)
     g.close()
     ctx.close()
+
+
+def test_l2_window_keeps_results(agis):
+    """The persisting-L2 window over the hub bitmaps is a cache hint: estimates (plain,
+    batched, with and without epoch tails) and sampler tile sums are the same bits
+    with the default window, a small one and none."""
+    ctx = agis.Context(0)
+    off, cols = I.rmat_graph(13, 16, seed=6)
+    g = agis.Graph(ctx, off, cols)
+    g.set_memory_policy(bitmap_min_degree=64)        # hub bitmaps on this small graph
+    g.preprocess(1, 2.0 ** -10)
+    pats = [agis.Pattern(*I.PATTERNS[n]) for n in ("4-clique", "house", "5-cycle")]
+    T = agis.TILE
+    opts = [agis.default_opts(mode=m, seed=40 + m, eps=0.0, max_trials=1000 * T, chunk_trials=1000 * T)
+            for m in range(3)]
+    keys = ("hits", "sectors", "sectors_streamed", "sectors_survey", "sum_x", "sum_x2")
+    runs = []
+    for nbytes in (48 << 20, 1 << 20, 0):
+        g.set_l2_window(nbytes)
+        single = [agis.estimate(g, p, o) for p, o in zip(pats, opts)]
+        batch = agis.estimate_batch(g, pats, opts)
+        sums = [_device_tile_sums(agis, g, p, o, 64) for p, o in zip(pats, opts)]
+        runs.append((single, batch, sums))
+    for single, batch, sums in runs[1:]:
+        for a, b in zip(runs[0][0] + runs[0][1] + runs[0][2], single + batch + sums):
+            for key in keys:
+                assert a[key] == b[key], key
+    g.close()
+    ctx.close()
