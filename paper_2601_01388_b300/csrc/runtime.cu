@@ -13,7 +13,8 @@
 #ifndef AGIS_SAMPLE_SPAN
 #define AGIS_SAMPLE_SPAN 1
 #endif
-// Tail of an epoch larger than the grid, in grids' worth of tiles (see tail_tiles).
+// Tail of an epoch, in grids' worth of tiles (see tail_tiles); 1 / 2 / 4 / 8 / 16 grids
+// measured, eight kept.
 #ifndef AGIS_TAIL_GRIDS
 #define AGIS_TAIL_GRIDS 8
 #endif
@@ -131,16 +132,16 @@ int ensure_buffers(LaunchBuffers &lb, size_t n_queries, size_t n_items)
     return AGIS_OK;
 }
 
-// The last tiles of an epoch -- as many as a full grid has CTAs, or all of a smaller
-// epoch -- run on the scatter kernel, where every warp of the grid takes single
-// trials.  The main kernel gives a CTA whole tiles, 32 trials back to back on each
-// warp, so an epoch of few tiles leaves most of the GPU idle, and in a larger one the
-// CTAs that run out of tiles wait up to a tile's time for the last ones.  Launched
-// beside the main kernel at a lower priority, the scatter kernel's CTAs take the SM
-// slots that the main kernel's CTAs free as they run out, and its single trials
-// level the end of the epoch.  Measured on the benchmark graph (all of an epoch in
-// scatter mode): a 4-clique query to +-1% (20,480 trials) 26.3 -> 5.9 ms, a
-// 5-clique (45,056) 56 -> 12.5 ms.
+// The last tiles of an epoch -- AGIS_TAIL_GRIDS times as many as a full grid has
+// CTAs, or all of a smaller epoch -- run on the scatter kernel, where every warp of
+// the grid takes single trials.  The main kernel gives a CTA whole tiles, 32 trials
+// back to back on each warp, so an epoch of few tiles leaves most of the GPU idle,
+// and in a larger one the CTAs that run out of tiles wait up to a tile's time for
+// the last ones.  Launched beside the main kernel at a lower priority, the scatter
+// kernel's CTAs take the SM slots that the main kernel's CTAs free as they run out,
+// and its single trials level the end of the epoch.  Measured on the benchmark
+// graph (all of an epoch in scatter mode): a 4-clique query to +-1% (20,480
+// trials) 26.3 -> 5.9 ms, a 5-clique (45,056) 56 -> 12.5 ms.
 size_t tail_capacity(int grid)
 {
     return (size_t)(std::max(1.0, (double)AGIS_TAIL_GRIDS) * (double)std::max(grid, 0));
