@@ -106,3 +106,29 @@ def test_layout_constants_match_header(agis):
             fields += [n.strip() for n in " ".join(words[1:]).split(",")]
     assert fields == [f for f, _ in agis.Result._fields_]
     assert ctypes.sizeof(agis.Result) == 120     # 15 eight-byte slots, no padding
+
+
+def test_null_handles_are_argument_errors(agis):
+    """Every call named here checks its handles before touching the device, so a NULL
+    handle is ARG (include/agis.h) on any host, with or without a GPU."""
+    import ctypes
+    lib = agis._lib
+    res = agis.Result()
+    opts = agis.default_opts()
+    out = ctypes.c_void_p()
+    fp = ctypes.c_uint64()
+    calls = [
+        ("agis_destroy", (None,)),
+        ("agis_graph_free", (None,)),
+        ("agis_graph_preprocess", (None, 1, 2.0 ** -10)),
+        ("agis_graph_set_memory_policy", (None, 0, 0, 0, 0)),
+        ("agis_graph_set_l2_window", (None, 1 << 20)),
+        ("agis_graph_drop_tables", (None,)),
+        ("agis_graph_orient", (None, ctypes.byref(out))),
+        ("agis_graph_is_oriented", (None,)),
+        ("agis_graph_fingerprint", (None, ctypes.byref(fp))),
+        ("agis_estimate", (None, None, ctypes.byref(opts), ctypes.byref(res))),
+        ("agis_server_destroy", (None,)),
+    ]
+    for name, args in calls:
+        assert getattr(lib, name)(*args) == agis.ERR_ARG, name
