@@ -305,9 +305,10 @@ int agis_pattern_free(agis_pattern *p);
 int agis_estimate(agis_graph *g, const agis_pattern *p, const agis_opts *opts,
                   agis_result *out);
 
-/* agis_estimate_batch: n queries (patterns[i], opts[i]) in one persistent,
- * work-stealing launch per epoch, replayed from a captured CUDA graph; tiles of
- * all unconverged queries share each launch.  Each out[i] equals what
+/* agis_estimate_batch: n queries (patterns[i], opts[i]) in one replayed CUDA graph
+ * per epoch: a persistent, work-stealing sampler launch, with the epoch's last
+ * tiles (all of a short epoch) on a launch where every warp takes single trials;
+ * tiles of all unconverged queries share each epoch.  Each out[i] equals what
  * agis_estimate(g, patterns[i], &opts[i]) returns.  Errors: as agis_estimate. */
 int agis_estimate_batch(agis_graph *g, int n, const agis_pattern *const *patterns,
                         const agis_opts *opts, agis_result *out);
@@ -405,7 +406,7 @@ double agis_z_of_delta(double delta);
  * A server keeps the graph resident and runs a scheduler thread that admits
  * queries while a slot is free and their weight tables fit in scratch_bytes of
  * device memory, runs all admitted queries together in epochs (each epoch one
- * persistent launch over every admitted query's next tiles), retires queries at
+ * replayed CUDA graph over every admitted query's next tiles), retires queries at
  * their first converged checkpoint and admits waiting ones as slots and memory
  * free up (continuous batching).  Two epochs are in flight at a time: the next one
  * is staged and enqueued while the current one runs, so queries that arrive while
